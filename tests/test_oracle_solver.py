@@ -1,0 +1,107 @@
+"""Pins for oracle/krylov.py, oracle/precond.py and oracle/solve.py (Section II.B, Eq. 10)."""
+import numpy as np
+import pytest
+
+from oracle import krylov, mvm, precond, solve
+from paper_2501_13512_gb300 import inputs
+
+K0 = 2 * np.pi
+H = 0.05
+
+
+def test_bicgstab_matches_dense_solve():
+    eps_r, _, b = inputs.random_case((4, 4, 3), seed=21)
+    A = mvm.dense_operator(eps_r, H, K0)
+    xref = np.linalg.solve(A, b.ravel()).reshape(b.shape)
+    op = mvm.FFTOperator(eps_r, H, K0)
+    x, info = krylov.bicgstab(op.apply, b, tol=1e-11, maxit=500)
+    assert info["status"] == krylov.CONVERGED
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(x - xref) <= 10 * kappa * 1e-11 * np.linalg.norm(xref)
+    r = np.linalg.norm(b - op(x)) / np.linalg.norm(b)
+    assert r <= 1e-10
+
+
+def test_bicgstab_zero_rhs_and_identity():
+    b = np.zeros((3, 2, 2, 2), complex)
+    x, info = krylov.bicgstab(lambda v: v, b, 1e-6, 10)
+    assert info["status"] == krylov.CONVERGED and not np.any(x)
+    b = np.ones((3, 2, 2, 2), complex)
+    x, info = krylov.bicgstab(lambda v: 2 * v, b, 1e-12, 10)
+    assert info["iters"] == 0.5 and np.allclose(x, 0.5 * b, rtol=1e-15)
+
+
+def test_block_inverse_matches_dense_lu():
+    eps_r, bid, x = inputs.random_case((6, 5, 4), seed=3, block_grid=(3, 3, 2))
+    P = precond.BlockPreconditioner(eps_r, bid, H, K0, inner_tol=1e-13, inner_maxit=400)
+    y = P(x)
+    A = mvm.dense_operator(eps_r, H, K0)
+    fb = np.tile(bid.ravel(), 3)
+    yref = x.ravel().copy()
+    for blk in P.blocks:
+        idx = np.nonzero(fb == blk.bid)[0]
+        yref[idx] = np.linalg.solve(A[np.ix_(idx, idx)], x.ravel()[idx])
+    assert np.linalg.norm(y.ravel() - yref) <= 1e-10 * np.linalg.norm(yref)
+
+
+def test_inexact_block_inverse_within_inner_tolerance():
+    eps_r, bid, x = inputs.random_case((6, 5, 4), seed=8, block_grid=(3, 5, 4))
+    tol = 1e-2
+    P = precond.BlockPreconditioner(eps_r, bid, H, K0, inner_tol=tol)
+    y = P(x)
+    A = mvm.dense_operator(eps_r, H, K0)
+    fb = np.tile(bid.ravel(), 3)
+    for blk in P.blocks:
+        idx = np.nonzero(fb == blk.bid)[0]
+        Ak = A[np.ix_(idx, idx)]
+        res = np.linalg.norm(x.ravel()[idx] - Ak @ y.ravel()[idx]) / np.linalg.norm(x.ravel()[idx])
+        assert res <= tol
+
+
+def test_single_block_is_exact_inverse():
+    # K2 = A when one block holds every voxel: the outer solve stops at its first half-step.
+    eps_r, _, b = inputs.random_case((5, 4, 3), seed=9)
+    bid = np.zeros(eps_r.shape, np.int32)
+    E, info = solve.solve(eps_r, bid, H, K0, b, tol=1e-6, use_precond=True,
+                          inner_tol=1e-12, inner_maxit=500)
+    assert info["iters"] == 0.5
+    assert info["true_rel_res"] <= 1e-6
+
+
+def test_preconditioned_and_plain_agree():
+    eps_r, bid, b = inputs.random_case((6, 6, 4), seed=13, block_grid=(3, 3, 4))
+    E1, i1 = solve.solve(eps_r, bid, H, K0, b, tol=1e-10, use_precond=True, inner_tol=1e-2)
+    E0, i0 = solve.solve(eps_r, bid, H, K0, b, tol=1e-10, use_precond=False)
+    assert i1["true_rel_res"] <= 1e-9 and i0["true_rel_res"] <= 1e-9
+    assert np.linalg.norm(E1 - E0) <= 1e-7 * np.linalg.norm(E0)
+
+
+def test_absorbed_power_nonnegative():
+    w = inputs.sphere(n=10, eps=3.0 - 0.5j, voxels_per_wl=20)
+    ein = solve.plane_wave(w.n, w.h, w.k0, w.khat, w.pol)
+    E, info = solve.solve(w.eps_r, w.block_id, w.h, w.k0, ein, tol=1e-8, use_precond=False)
+    assert info["true_rel_res"] <= 1e-7
+    assert solve.absorbed_power(E, w.eps_r) > 0
+
+
+def test_optical_theorem_soft():
+    # extinction (forward amplitude) ~ scattering + absorption; the discrete
+    # system satisfies it only approximately, so this is a loose check.
+    w = inputs.sphere(n=12, eps=2.25 - 0.2j, voxels_per_wl=24)
+    k = w.k0
+    ein = solve.plane_wave(w.n, w.h, k, w.khat, w.pol)
+    E, _ = solve.solve(w.eps_r, w.block_id, w.h, k, ein, tol=1e-10, use_precond=False)
+    X, Y, Z = solve.voxel_positions(w.n, w.h)
+    chi = w.eps_r - 1
+    P = np.array([np.sum(chi * E[c] * np.exp(1j * k * Z)) for c in range(3)]) * w.h ** 3
+    # exp(+jwt): C_ext = -k Im(conj(E0) . P), P projected on the incident wave
+    c_ext = -k * np.imag(P[0])
+    th = np.linspace(0, np.pi, 121)
+    ph = np.linspace(0, 2 * np.pi, 121, endpoint=False)
+    T, F = np.meshgrid(th, ph, indexing="ij")
+    rh = np.stack([np.sin(T) * np.cos(F), np.sin(T) * np.sin(F), np.cos(T)], -1).reshape(-1, 3)
+    s = solve.far_field_rcs(E, w.eps_r, w.h, k, rh).reshape(T.shape) / (4 * np.pi)
+    c_sca = np.sum(s * np.sin(T)) * (th[1] - th[0]) * (ph[1] - ph[0])
+    c_abs = k * np.sum(-np.imag(w.eps_r) * np.sum(np.abs(E) ** 2, 0)) * w.h ** 3
+    assert c_ext > 0
+    assert abs(c_ext - (c_sca + c_abs)) <= 0.1 * c_ext
