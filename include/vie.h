@@ -1,0 +1,196 @@
+/*
+ * vie.h -- C ABI of the GB300 VIE-FFT engine (libvie.so).
+ *
+ * The engine solves the volume integral equation of Section II.A (Eq. 4,
+ * written in the total field E with chi = eps_r - 1):
+ *
+ *     (A E)_i = E_i - sum_j K(i - j) chi_j E_j = E_inc,i
+ *
+ * on a uniform Cartesian voxel grid, with K(D) = k0^2 G(D h) h^3 for D != 0
+ * (G the dyadic Green's function of Eq. 1) and K(0) = s_self I (equivalent
+ * sphere self term). Every product A x runs through the Toeplitz-to-circulant
+ * FFT embedding (Section I), and the solver is BiCGSTAB right-preconditioned
+ * with the block-diagonal matrix of Eq. 10, whose blocks are solved by inner
+ * BiCGSTAB-FFT iterations to a loose tolerance (Section II.B).
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns VIE_OK (0) or one of the VIE_E* codes;
+ *     vie_last_error() gives a text for the last failure on this thread.
+ *   - Vectors: caller-owned DEVICE memory on the device that was current when
+ *     the grid was created; complex interleaved (re, im); layout
+ *     [3][nz][ny][nx] (component x, y, z; x fastest). VIE_C128 vectors are
+ *     double pairs (16 B per entry), VIE_C64 vectors float pairs (8 B).
+ *   - Streams: work is enqueued on the given cudaStream_t (NULL = legacy
+ *     default stream). Functions that iterate (precond apply, solve) read
+ *     convergence flags back to the host and therefore return only when the
+ *     result is complete; vie_matvec, vie_plane_wave and vie_green_spectrum
+ *     are asynchronous with respect to the host.
+ *   - Handles (vie_grid, vie_spectrum) are opaque and owned by the library;
+ *     the library allocates its own device workspace at grid creation.
+ *   - Time convention exp(+j w t): a passive medium has Im(eps_r) <= 0.
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* vie_stream_t; /* identical to cudaStream_t */
+
+enum vie_status {
+    VIE_OK = 0,
+    VIE_EINVAL = 1,      /* invalid argument (null pointer, bad size, aliasing)  */
+    VIE_ENOMEM = 2,      /* device or host allocation failed                    */
+    VIE_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed         */
+    VIE_ENOTCONV = 4,    /* iteration limit reached; result and stats are valid */
+    VIE_EBREAKDOWN = 5,  /* BiCGSTAB breakdown: rho, <rhat,v> or <t,t> is 0/NaN */
+    VIE_ETIMEOUT = 6,    /* a bounded wait for the device gave up               */
+    VIE_EBUSY = 7        /* admission refused: not enough free device memory    */
+};
+
+enum vie_precision {
+    VIE_C128 = 1,        /* complex double: FP64 FFTs and arithmetic            */
+    VIE_C64 = 2          /* complex float: FP32 FFTs, FP64 reductions/scalars   */
+};
+
+enum vie_solve_mode {
+    VIE_MODE_PLAIN_C128 = 0, /* every MVM, inner solve and vector op in complex128 */
+    VIE_MODE_MIXED = 1       /* FP64 true residuals + complex64 preconditioned
+                                correction solves (iterative refinement)          */
+};
+
+typedef struct vie_grid vie_grid;
+typedef struct vie_spectrum vie_spectrum;
+
+/* Problem geometry (Section II.A: uniform hexahedral mesh; Eq. 10 blocks). */
+typedef struct {
+    int32_t nx, ny, nz;      /* voxels per axis, each in [1, 512]                    */
+    double h;                /* voxel edge (same length unit as 2*pi/k0)             */
+    const double* eps_r;     /* HOST, 2*nx*ny*nz doubles: relative permittivity
+                                (re, im) per voxel, [nz][ny][nx]; copied             */
+    const int32_t* block_id; /* HOST, nx*ny*nz: subdomain of each voxel for the
+                                block-diagonal preconditioner, -1 = no block
+                                (identity); any non-negative ids; NULL = all -1;
+                                copied                                               */
+    uint32_t flags;          /* reserved, must be 0                                  */
+} vie_grid_desc;
+
+typedef struct {
+    int32_t nblocks;         /* non-empty blocks found in block_id                 */
+    int32_t ngroups;         /* batches of blocks sharing one padded FFT shape     */
+    int32_t Mx, My, Mz;      /* padded FFT shape of the full-grid operator         */
+    int64_t device_bytes;    /* device memory held by the grid handle              */
+} vie_grid_info;
+
+/* Creates the grid on the current CUDA device: uploads chi = eps_r - 1,
+ * partitions the blocks (Eq. 10) into groups that share a padded FFT shape,
+ * and allocates all workspace. Errors: VIE_EINVAL (sizes, flags, nulls),
+ * VIE_ENOMEM, VIE_ECUDA. */
+int vie_grid_create(const vie_grid_desc* desc, vie_grid** out);
+
+/* Waits for the grid's device, then frees the grid and its workspace. Every
+ * spectrum of the grid must have been released first. Errors: VIE_EINVAL. */
+int vie_grid_destroy(vie_grid* grid);
+
+/* Block count, group count, padded FFT shape and device bytes of a grid. */
+int vie_grid_get_info(const vie_grid* grid, vie_grid_info* info);
+
+/* Green-tensor spectra (Eq. 1, sampled at lattice offsets, self term at 0):
+ * computes in FP64 on the device the 3D FFT of the six components of K for
+ * the full grid and for every block group, at wavenumber k0 > 0.
+ * precision_mask: VIE_C128, VIE_C64 or both (bitwise or); the complex64 copy
+ * is rounded from the FP64 spectrum. The spectrum belongs to the grid and must
+ * be released before the grid is destroyed. Asynchronous on `stream`.
+ * Errors: VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA. */
+int vie_green_spectrum(vie_grid* grid, double k0, int precision_mask,
+                       vie_stream_t stream, vie_spectrum** out);
+
+/* Waits for the device, then frees the spectra. Errors: VIE_EINVAL. */
+int vie_spectrum_release(vie_spectrum* spectrum);
+
+/* Incident plane wave E_inc = pol * exp(-j k0 khat . r) at voxel centres
+ * r = (i + 1/2) h - (grid centre). khat: 3 doubles (unit propagation
+ * direction); pol: 6 doubles, complex polarisation (re, im) per component.
+ * Writes one vector of `precision` to einc_dev. Asynchronous. */
+int vie_plane_wave(const vie_grid* grid, double k0, const double* khat,
+                   const double* pol, int precision, void* einc_dev,
+                   vie_stream_t stream);
+
+/* y = A x = x - G(chi x) (Eq. 4; FFT-accelerated MVM of Section I) with the
+ * spectrum's k0, in `precision` (the spectrum must hold it). x and y must not
+ * overlap (VIE_EINVAL). Asynchronous. */
+int vie_matvec(vie_grid* grid, const vie_spectrum* spectrum, int precision,
+               const void* x_dev, void* y_dev, vie_stream_t stream);
+
+typedef struct {
+    int32_t nblocks;         /* blocks solved                                       */
+    int32_t max_iters;       /* largest inner BiCGSTAB iteration count              */
+    double mean_iters;       /* mean inner iteration count (half-steps as 0.5)      */
+    int32_t not_converged;   /* blocks that hit inner_maxit (not an error)          */
+    int32_t breakdowns;      /* blocks whose inner BiCGSTAB broke down              */
+} vie_precond_stats;
+
+/* y = K2^{-1} b with K2 = diag(A_1, ..., A_N) (Eq. 10): for each block k the
+ * system A_k x_k = b|S_k (rows/columns of A on the block's voxels, all three
+ * components, Eq. 11) is solved by BiCGSTAB-FFT from x_k = 0 to
+ * ||b_k - A_k x_k|| <= inner_tol ||b_k|| or inner_maxit iterations; y = b on
+ * voxels of no block. All blocks of all groups are iterated together in
+ * batched launches. b and y are vectors of `precision` and must not overlap.
+ * stats may be NULL. Synchronous with the host at return. */
+int vie_block_precond_apply(vie_grid* grid, const vie_spectrum* spectrum,
+                            int precision, const void* b_dev, void* y_dev,
+                            double inner_tol, int inner_maxit,
+                            vie_stream_t stream, vie_precond_stats* stats);
+
+typedef struct {
+    double outer_tol;        /* stop when ||E_inc - A E|| <= outer_tol ||E_inc||   */
+    double inner_tol;        /* block solves' relative tolerance (Section II.B)     */
+    int32_t outer_maxit;     /* outer BiCGSTAB iterations (per refinement in MIXED) */
+    int32_t inner_maxit;     /* inner BiCGSTAB iterations per block apply           */
+    int32_t use_precond;     /* 0: unpreconditioned BiCGSTAB                        */
+    int32_t mode;            /* vie_solve_mode                                      */
+    int32_t max_refinements; /* MIXED: FP64 residual corrections, 0 = default (8)   */
+    double wait_timeout_ms;  /* bound on each host wait for the device, 0 = 60000   */
+} vie_solve_opts;
+
+typedef struct {
+    double outer_iters;      /* outer BiCGSTAB iterations (half-steps as 0.5),
+                                summed over refinements in MIXED                    */
+    int64_t inner_iters;     /* inner BiCGSTAB iterations summed over all blocks    */
+    int32_t precond_applies; /* K2^{-1} applications                                */
+    int32_t matvecs_c128;    /* full-grid MVMs in complex128                        */
+    int32_t matvecs_c64;     /* full-grid MVMs in complex64                         */
+    int32_t refinements;     /* MIXED: FP64 residual evaluations after the first    */
+    double true_rel_res;     /* ||E_inc - A E|| / ||E_inc||, FP64, at exit          */
+    int32_t status;          /* same value as returned                              */
+} vie_solve_stats;
+
+/* Solves A E = E_inc (Eq. 4) by right-preconditioned BiCGSTAB (Section II.B).
+ * VIE_MODE_PLAIN_C128: one BiCGSTAB in complex128 throughout.
+ * VIE_MODE_MIXED: FP64 residual r = E_inc - A E (complex128 MVM), then a
+ *   complex64 preconditioned BiCGSTAB for A d = r with FP64 reductions and
+ *   scalars, E += d, repeated until the FP64 residual meets outer_tol.
+ * einc_dev, e_dev: complex128 vectors (caller-owned, distinct). The spectrum
+ * must hold VIE_C128, and VIE_C64 too for MIXED. Returns VIE_OK,
+ * VIE_ENOTCONV (E and stats still valid), VIE_EBREAKDOWN, VIE_ETIMEOUT,
+ * VIE_EINVAL, VIE_ECUDA. stats may be NULL. */
+int vie_solve(vie_grid* grid, const vie_spectrum* spectrum, const void* einc_dev,
+              void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
+              vie_solve_stats* stats);
+
+/* Copies the text of the last error on this thread into buf (NUL-terminated,
+ * truncated to len). Returns the length of the full message. */
+int vie_last_error(char* buf, size_t len);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int vie_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIE_H */

@@ -1,0 +1,733 @@
+// C ABI of libvie: handle management and the host-side drivers of the
+// block-preconditioned BiCGSTAB-FFT solver (Section II.B, Eq. 10).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
+
+#include "vie_internal.cuh"
+
+namespace vie {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    std::string m = std::string(what) + " failed: " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) + ")";
+    if (e == cudaErrorMemoryAllocation) return fail(VIE_ENOMEM, m);
+    return fail(VIE_ECUDA, m);
+}
+
+// ---------------------------------------------------------------- twiddles (per device)
+static std::mutex g_tw_mutex;
+static std::map<int, Twiddles> g_tw;
+
+int get_twiddles(Twiddles* out) {
+    int dev = 0;
+    VIE_CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_tw_mutex);
+    auto it = g_tw.find(dev);
+    if (it != g_tw.end()) {
+        *out = it->second;
+        return VIE_OK;
+    }
+    // W^m = exp(-2 pi i m / Lmax), evaluated in long double and rounded once.
+    std::vector<double2> h128(kLmax);
+    std::vector<float2> h64(kLmax);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int m = 0; m < kLmax; ++m) {
+        long double th = 2.0L * pi * (long double)m / (long double)kLmax;
+        long double c = cosl(th), s = -sinl(th);
+        h128[m] = make_double2((double)c, (double)s);
+        h64[m] = make_float2((float)c, (float)s);
+    }
+    Twiddles t;
+    VIE_CK(cudaMalloc(&t.d128, kLmax * sizeof(double2)));
+    VIE_CK(cudaMalloc(&t.d64, kLmax * sizeof(float2)));
+    VIE_CK(cudaMemcpy(t.d128, h128.data(), kLmax * sizeof(double2), cudaMemcpyHostToDevice));
+    VIE_CK(cudaMemcpy(t.d64, h64.data(), kLmax * sizeof(float2), cudaMemcpyHostToDevice));
+    g_tw[dev] = t;
+    *out = t;
+    return VIE_OK;
+}
+
+// ---------------------------------------------------------------- allocation
+template <class T>
+static int dalloc(vie_grid* g, T** p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) return VIE_OK;
+    size_t bytes = (size_t)count * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VIE_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    g->allocations.push_back((void*)*p);
+    g->device_bytes += (int64_t)bytes;
+    return VIE_OK;
+}
+
+static int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+static int ilog2i(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+// Smallest power of two >= 2b - 1: embeds offsets -(b-1) .. b-1 circularly.
+static int padded_len(int b) { return next_pow2(2 * b - 1); }
+
+static void set_shape(BoxSet& bs, int bx, int by, int bz) {
+    bs.bx = bx; bs.by = by; bs.bz = bz;
+    bs.Mx = padded_len(bx); bs.My = padded_len(by); bs.Mz = padded_len(bz);
+    bs.lx = ilog2i(bs.Mx); bs.ly = ilog2i(bs.My); bs.lz = ilog2i(bs.Mz);
+}
+
+template <class C>
+static int alloc_krylov(vie_grid* g, KrylovVecs<C>& k, int64_t n, bool with_bx, bool with_yz) {
+    if (with_bx) {
+        VIE_TRY(dalloc(g, &k.b, n));
+        VIE_TRY(dalloc(g, &k.x, n));
+    }
+    VIE_TRY(dalloc(g, &k.r, n));
+    VIE_TRY(dalloc(g, &k.rhat, n));
+    VIE_TRY(dalloc(g, &k.p, n));
+    VIE_TRY(dalloc(g, &k.v, n));
+    VIE_TRY(dalloc(g, &k.s, n));
+    VIE_TRY(dalloc(g, &k.t, n));
+    if (with_yz) {
+        VIE_TRY(dalloc(g, &k.y, n));
+        VIE_TRY(dalloc(g, &k.z, n));
+    } else {
+        k.y = k.p;   // no preconditioner: y = p, z = s
+        k.z = k.s;
+    }
+    return VIE_OK;
+}
+
+static int alloc_reduce(vie_grid* g, ReduceScratch& red, int nseg) {
+    red.nseg = nseg;
+    VIE_TRY(dalloc(g, &red.part, (int64_t)nseg * kMaxCtaPerSeg * 2));
+    VIE_TRY(dalloc(g, &red.count, nseg));
+    VIE_TRY(dalloc(g, &red.n_active, 1));
+    VIE_CK(cudaMemset(red.count, 0, nseg * sizeof(unsigned)));
+    VIE_CK(cudaMemset(red.n_active, 0, sizeof(int)));
+    return VIE_OK;
+}
+
+static int alloc_fft_work(vie_grid* g, BoxSet& bs) {
+    int64_t w1 = (int64_t)bs.nb * 3 * bs.bz * bs.by * bs.Mx;
+    int64_t w2 = (int64_t)bs.nb * 3 * bs.bz * bs.My * bs.Mx;
+    double2* p1 = nullptr;
+    double2* p2 = nullptr;
+    VIE_TRY(dalloc(g, &p1, w1));
+    VIE_TRY(dalloc(g, &p2, w2));
+    bs.w1 = p1;
+    bs.w2 = p2;
+    return VIE_OK;
+}
+
+static int upload_chi(vie_grid* g, BoxSet& bs, const std::vector<double2>& chi) {
+    int64_t n = (int64_t)chi.size();
+    VIE_TRY(dalloc(g, &bs.chi128, n));
+    VIE_TRY(dalloc(g, &bs.chi64, n));
+    std::vector<float2> c64(n);
+    for (int64_t i = 0; i < n; ++i) c64[i] = make_float2((float)chi[i].x, (float)chi[i].y);
+    VIE_CK(cudaMemcpy(bs.chi128, chi.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+    VIE_CK(cudaMemcpy(bs.chi64, c64.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    return VIE_OK;
+}
+
+static void release_grid(vie_grid* g) {
+    for (void* p : g->allocations) cudaFree(p);
+    g->allocations.clear();
+    if (g->h_ring) cudaFreeHost(g->h_ring);
+    for (int i = 0; i < 2; ++i)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    delete g;
+}
+
+// Bounded host wait for an event (no device-side spin exists in this library;
+// the bound protects callers from a device that stopped answering).
+static int wait_event(cudaEvent_t ev, double timeout_ms) {
+    if (timeout_ms <= 0) timeout_ms = 60000.0;
+    auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return VIE_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery", __FILE__, __LINE__);
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_ms) return fail(VIE_ETIMEOUT, "device did not finish within the wait bound");
+    }
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+extern "C" int vie_version(void) { return 100; }
+
+extern "C" int vie_last_error(char* buf, size_t len) {
+    if (buf && len) {
+        size_t n = std::min(len - 1, g_last_error.size());
+        memcpy(buf, g_last_error.data(), n);
+        buf[n] = 0;
+    }
+    return (int)g_last_error.size();
+}
+
+extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
+    if (!d || !out) return fail(VIE_EINVAL, "vie_grid_create: null argument");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nx > kLmax / 2 || d->ny > kLmax / 2 || d->nz > kLmax / 2)
+        return fail(VIE_EINVAL, "vie_grid_create: each of nx, ny, nz must be in [1, 512]");
+    if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(VIE_EINVAL, "vie_grid_create: h must be positive");
+    if (!d->eps_r) return fail(VIE_EINVAL, "vie_grid_create: eps_r is null");
+    if (d->flags != 0) return fail(VIE_EINVAL, "vie_grid_create: flags must be 0");
+
+    vie_grid* g = new vie_grid();
+    auto bail = [&](int rc) { release_grid(g); return rc; };
+    if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(VIE_ECUDA, "no CUDA device"));
+    g->nx = d->nx; g->ny = d->ny; g->nz = d->nz; g->h = d->h;
+    const int64_t N = (int64_t)d->nx * d->ny * d->nz;
+    g->N = N;
+
+    // contrast chi = eps_r - 1 (Eq. 2: J = j w eps0 chi E)
+    std::vector<double2> chi(N);
+    for (int64_t i = 0; i < N; ++i) {
+        double re = d->eps_r[2 * i], im = d->eps_r[2 * i + 1];
+        if (!std::isfinite(re) || !std::isfinite(im)) return bail(fail(VIE_EINVAL, "vie_grid_create: non-finite eps_r"));
+        chi[i] = make_double2(re - 1.0, im);
+    }
+    g->full.nb = 1;
+    set_shape(g->full, d->nx, d->ny, d->nz);
+    int rc = upload_chi(g, g->full, chi);
+    if (rc) return bail(rc);
+    if ((rc = alloc_fft_work(g, g->full))) return bail(rc);
+
+    // blocks of Eq. 10: compact ids in increasing order of the user's ids
+    std::vector<int32_t> bid(N, -1);
+    std::map<int32_t, int> ids;
+    if (d->block_id) {
+        for (int64_t i = 0; i < N; ++i)
+            if (d->block_id[i] >= 0) ids.emplace(d->block_id[i], 0);
+        int k = 0;
+        for (auto& kv : ids) kv.second = k++;
+        for (int64_t i = 0; i < N; ++i)
+            if (d->block_id[i] >= 0) bid[i] = ids[d->block_id[i]];
+    }
+    const int K = (int)ids.size();
+    g->nblocks = K;
+    std::vector<int> lo(3 * K, INT32_MAX), hi(3 * K, -1);
+    for (int z = 0; z < g->nz; ++z)
+        for (int y = 0; y < g->ny; ++y)
+            for (int x = 0; x < g->nx; ++x) {
+                int b = bid[((int64_t)z * g->ny + y) * g->nx + x];
+                if (b < 0) continue;
+                int c[3] = {x, y, z};
+                for (int a = 0; a < 3; ++a) {
+                    lo[3 * b + a] = std::min(lo[3 * b + a], c[a]);
+                    hi[3 * b + a] = std::max(hi[3 * b + a], c[a]);
+                }
+            }
+    // group blocks by padded FFT shape of their bounding boxes
+    std::map<std::tuple<int, int, int>, std::vector<int>> bykey;
+    for (int b = 0; b < K; ++b) {
+        int ext[3];
+        for (int a = 0; a < 3; ++a) ext[a] = hi[3 * b + a] - lo[3 * b + a] + 1;
+        bykey[std::make_tuple(padded_len(ext[2]), padded_len(ext[1]), padded_len(ext[0]))].push_back(b);
+    }
+    std::vector<int32_t> h_group(K), h_index(K), h_origin(3 * K);
+    g->groups.resize(bykey.size());
+    int gi = 0;
+    for (auto& kv : bykey) {
+        Group& gr = g->groups[gi];
+        const std::vector<int>& mem = kv.second;
+        int mx = 1, my = 1, mz = 1;
+        for (int b : mem) {
+            mx = std::max(mx, hi[3 * b] - lo[3 * b] + 1);
+            my = std::max(my, hi[3 * b + 1] - lo[3 * b + 1] + 1);
+            mz = std::max(mz, hi[3 * b + 2] - lo[3 * b + 2] + 1);
+        }
+        gr.bs.nb = (int)mem.size();
+        set_shape(gr.bs, mx, my, mz);
+        gr.bs.block_ids = mem;
+        const int64_t box = gr.bs.box_elems();
+        std::vector<double2> gchi(gr.bs.nb * box, make_double2(0, 0));
+        std::vector<uint8_t> gmask(gr.bs.nb * box, 0);
+        std::vector<int32_t> gorig(3 * gr.bs.nb);
+        for (int j = 0; j < gr.bs.nb; ++j) {
+            int b = mem[j];
+            h_group[b] = gi;
+            h_index[b] = j;
+            for (int a = 0; a < 3; ++a) gorig[3 * j + a] = h_origin[3 * b + a] = lo[3 * b + a];
+            for (int lz = 0; lz < mz; ++lz)
+                for (int ly = 0; ly < my; ++ly)
+                    for (int lx = 0; lx < mx; ++lx) {
+                        int x = lo[3 * b] + lx, y = lo[3 * b + 1] + ly, z = lo[3 * b + 2] + lz;
+                        if (x >= g->nx || y >= g->ny || z >= g->nz) continue;
+                        int64_t gv = ((int64_t)z * g->ny + y) * g->nx + x;
+                        if (bid[gv] != b) continue;
+                        int64_t l = (int64_t)j * box + ((int64_t)lz * my + ly) * mx + lx;
+                        gmask[l] = 1;
+                        gchi[l] = chi[gv];
+                    }
+        }
+        if ((rc = upload_chi(g, gr.bs, gchi))) return bail(rc);
+        if ((rc = dalloc(g, &gr.bs.mask, gr.bs.nb * box))) return bail(rc);
+        if ((rc = dalloc(g, &gr.bs.origin, 3 * gr.bs.nb))) return bail(rc);
+        if (cudaMemcpy(gr.bs.mask, gmask.data(), gmask.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(gr.bs.origin, gorig.data(), gorig.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(VIE_ECUDA, "upload of block tables failed"));
+        if ((rc = alloc_fft_work(g, gr.bs))) return bail(rc);
+        const int64_t nv = gr.bs.nb * gr.bs.vec_elems();
+        if ((rc = alloc_krylov(g, gr.k128, nv, true, false))) return bail(rc);
+        if ((rc = alloc_krylov(g, gr.k64, nv, true, false))) return bail(rc);
+        if ((rc = dalloc(g, &gr.st, gr.bs.nb))) return bail(rc);
+        if ((rc = alloc_reduce(g, gr.red, gr.bs.nb))) return bail(rc);
+        ++gi;
+    }
+    if ((rc = dalloc(g, &g->block_id, N))) return bail(rc);
+    if (cudaMemcpy(g->block_id, bid.data(), N * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(VIE_ECUDA, "upload of block ids failed"));
+
+    // outer Krylov workspace (b and x are the caller's vectors in a solve)
+    const int64_t n3 = 3 * N;
+    if ((rc = alloc_krylov(g, g->o128, n3, false, true))) return bail(rc);
+    if ((rc = alloc_krylov(g, g->o64, n3, true, true))) return bail(rc);
+    if ((rc = dalloc(g, &g->tmp128, n3))) return bail(rc);
+    if ((rc = dalloc(g, &g->ost, 1))) return bail(rc);
+    if ((rc = alloc_reduce(g, g->ored, 1))) return bail(rc);
+    if ((rc = dalloc(g, &g->dscal, 8))) return bail(rc);
+    size_t ring = 2 * (g->groups.size() + 1) * sizeof(int) + sizeof(SegState) + 8 * sizeof(double);
+    if (cudaHostAlloc((void**)&g->h_ring, ring, cudaHostAllocDefault) != cudaSuccess)
+        return bail(fail(VIE_ENOMEM, "pinned host allocation failed"));
+    for (int i = 0; i < 2; ++i)
+        if (cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(VIE_ECUDA, "cudaEventCreate failed"));
+    *out = g;
+    return VIE_OK;
+}
+
+extern "C" int vie_grid_destroy(vie_grid* g) {
+    if (!g) return fail(VIE_EINVAL, "vie_grid_destroy: null grid");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    release_grid(g);
+    cudaSetDevice(prev);
+    return VIE_OK;
+}
+
+extern "C" int vie_grid_get_info(const vie_grid* g, vie_grid_info* info) {
+    if (!g || !info) return fail(VIE_EINVAL, "vie_grid_get_info: null argument");
+    info->nblocks = g->nblocks;
+    info->ngroups = (int32_t)g->groups.size();
+    info->Mx = g->full.Mx;
+    info->My = g->full.My;
+    info->Mz = g->full.Mz;
+    info->device_bytes = g->device_bytes;
+    return VIE_OK;
+}
+
+// ---------------------------------------------------------------- spectra
+extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t stream, vie_spectrum** out) {
+    if (!g || !out) return fail(VIE_EINVAL, "vie_green_spectrum: null argument");
+    *out = nullptr;
+    if (!(k0 > 0.0) || !std::isfinite(k0)) return fail(VIE_EINVAL, "vie_green_spectrum: k0 must be positive");
+    if (mask == 0 || (mask & ~(VIE_C128 | VIE_C64))) return fail(VIE_EINVAL, "vie_green_spectrum: bad precision mask");
+    cudaStream_t s = (cudaStream_t)stream;
+    vie_spectrum* sp = new vie_spectrum();
+    sp->grid = g;
+    sp->k0 = k0;
+    sp->precision_mask = mask;
+    auto bail = [&](int rc) {
+        for (auto p : sp->g128) cudaFree(p);
+        for (auto p : sp->g64) cudaFree(p);
+        delete sp;
+        return rc;
+    };
+    std::vector<const BoxSet*> sets;
+    sets.push_back(&g->full);
+    for (auto& gr : g->groups) sets.push_back(&gr.bs);
+    for (const BoxSet* bs : sets) {
+        const int64_t n = 6 * bs->spec_elems();
+        double2* G = nullptr;
+        if (cudaMalloc(&G, n * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(VIE_ENOMEM, "spectrum allocation failed"));
+        }
+        sp->g128.push_back(G);
+        int rc = green_sample(*bs, k0, g->h, G, s);
+        if (!rc) rc = spectrum_fft<double2>(*bs, G, s);
+        if (rc) return bail(rc);
+        float2* G64 = nullptr;
+        if (mask & VIE_C64) {
+            if (cudaMalloc(&G64, n * sizeof(float2)) != cudaSuccess) {
+                cudaGetLastError();
+                return bail(fail(VIE_ENOMEM, "spectrum allocation failed"));
+            }
+            if ((rc = convert_c128_to_c64(G, G64, n, s))) {
+                sp->g64.push_back(G64);
+                return bail(rc);
+            }
+        }
+        sp->g64.push_back(G64);
+    }
+    if (!(mask & VIE_C128)) {
+        // the FP64 spectrum was only the source of the complex64 copy
+        if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(VIE_ECUDA, "spectrum generation failed"));
+        for (auto& p : sp->g128) {
+            cudaFree(p);
+            p = nullptr;
+        }
+    }
+    *out = sp;
+    return VIE_OK;
+}
+
+extern "C" int vie_spectrum_release(vie_spectrum* sp) {
+    if (!sp) return fail(VIE_EINVAL, "vie_spectrum_release: null spectrum");
+    cudaDeviceSynchronize();
+    for (auto p : sp->g128)
+        if (p) cudaFree(p);
+    for (auto p : sp->g64)
+        if (p) cudaFree(p);
+    delete sp;
+    return VIE_OK;
+}
+
+namespace vie {
+
+template <class C> static const C* spec_of(const vie_spectrum* sp, int idx);
+template <> const double2* spec_of<double2>(const vie_spectrum* sp, int idx) { return sp->g128[idx]; }
+template <> const float2* spec_of<float2>(const vie_spectrum* sp, int idx) { return sp->g64[idx]; }
+template <class C> static KrylovVecs<C>& group_vecs(Group& gr);
+template <> KrylovVecs<double2>& group_vecs<double2>(Group& gr) { return gr.k128; }
+template <> KrylovVecs<float2>& group_vecs<float2>(Group& gr) { return gr.k64; }
+template <class C> static int prec_of();
+template <> int prec_of<double2>() { return VIE_C128; }
+template <> int prec_of<float2>() { return VIE_C64; }
+
+static int check_spectrum(const vie_grid* g, const vie_spectrum* sp, int precision) {
+    if (!sp || sp->grid != g) return fail(VIE_EINVAL, "spectrum does not belong to this grid");
+    if (precision != VIE_C128 && precision != VIE_C64) return fail(VIE_EINVAL, "precision must be VIE_C128 or VIE_C64");
+    if (!(sp->precision_mask & precision)) return fail(VIE_EINVAL, "spectrum was not generated in this precision");
+    return VIE_OK;
+}
+
+static bool overlaps(const void* a, const void* b, int64_t bytes) {
+    const char* pa = (const char*)a;
+    const char* pb = (const char*)b;
+    return pa < pb + bytes && pb < pa + bytes;
+}
+
+template <class C>
+static int mvm_full(vie_grid* g, const vie_spectrum* sp, const C* x, C* y, cudaStream_t s) {
+    return mvm_boxes<C>(g->full, spec_of<C>(sp, 0), x, y, nullptr, s);
+}
+
+// y = K2^{-1} b: all blocks of all groups iterate together; a block stops
+// when its own residual meets tol (or at maxit) and is skipped thereafter.
+template <class C>
+static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, double tol, int maxit,
+                         cudaStream_t s, vie_precond_stats* stats, double timeout_ms) {
+    const int64_t n3 = 3 * g->N;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (g->nblocks == 0) return vec_copy<C>(b, y, n3, s);
+    const int ng = (int)g->groups.size();
+    std::vector<Bicg<C>> bk(ng);
+    for (int i = 0; i < ng; ++i) {
+        Group& gr = g->groups[i];
+        KrylovVecs<C>& v = group_vecs<C>(gr);
+        VIE_TRY(precond_gather<C>(g, gr, b, v.b, s));
+        bk[i].nseg = gr.bs.nb;
+        bk[i].seglen = gr.bs.vec_elems();
+        bk[i].v = v;
+        bk[i].st = gr.st;
+        bk[i].red = &gr.red;
+        VIE_TRY(bicg_init<C>(bk[i], tol, maxit, s));
+    }
+    int* ring = (int*)g->h_ring;
+    for (int it = 0; it < maxit; ++it) {
+        const int slot = it & 1;
+        for (int i = 0; i < ng; ++i) {
+            Group& gr = g->groups[i];
+            Bicg<C>& k = bk[i];
+            const C* G = spec_of<C>(sp, 1 + i);
+            VIE_TRY(bicg_rho<C>(k, s));
+            VIE_TRY(bicg_update_p<C>(k, s));
+            VIE_TRY(mvm_boxes<C>(gr.bs, G, k.v.p, k.v.v, gr.st, s));
+            VIE_TRY(bicg_sigma<C>(k, s));
+            VIE_TRY(bicg_update_s<C>(k, s));
+            VIE_TRY(bicg_x_half<C>(k, s));
+            VIE_TRY(mvm_boxes<C>(gr.bs, G, k.v.s, k.v.t, gr.st, s));
+            VIE_TRY(bicg_omega<C>(k, s));
+            VIE_TRY(bicg_update_xr<C>(k, s));
+            VIE_CK(cudaMemcpyAsync(ring + slot * (ng + 1) + i, gr.red.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        }
+        VIE_CK(cudaEventRecord(g->ev[slot], s));
+        if (it > 0) {
+            // one iteration stays in flight while the previous one's counts are read
+            const int prev = slot ^ 1;
+            VIE_TRY(wait_event(g->ev[prev], timeout_ms));
+            int active = 0;
+            for (int i = 0; i < ng; ++i) active += ring[prev * (ng + 1) + i];
+            if (active == 0) break;
+        }
+    }
+    VIE_TRY(precond_copy_unblocked<C>(g, b, y, s));
+    for (int i = 0; i < ng; ++i) VIE_TRY(precond_scatter_group<C>(g, g->groups[i], group_vecs<C>(g->groups[i]).x, y, s));
+    if (stats) {
+        std::vector<SegState> hs;
+        double sum = 0.0;
+        stats->nblocks = g->nblocks;
+        for (int i = 0; i < ng; ++i) {
+            Group& gr = g->groups[i];
+            hs.resize(gr.bs.nb);
+            VIE_CK(cudaMemcpyAsync(hs.data(), gr.st, gr.bs.nb * sizeof(SegState), cudaMemcpyDeviceToHost, s));
+            VIE_CK(cudaEventRecord(g->ev[0], s));
+            VIE_TRY(wait_event(g->ev[0], timeout_ms));
+            for (auto& st : hs) {
+                sum += st.iters;
+                stats->max_iters = std::max(stats->max_iters, (int32_t)std::ceil(st.iters));
+                if (st.status == SEG_MAXIT) stats->not_converged++;
+                if (st.status == SEG_BREAKDOWN) stats->breakdowns++;
+            }
+        }
+        stats->mean_iters = sum / std::max(1, g->nblocks);
+    }
+    return VIE_OK;
+}
+
+static int read_outer_state(vie_grid* g, SegState* hs, cudaStream_t s, double timeout_ms) {
+    SegState* h = (SegState*)(g->h_ring + 2 * (g->groups.size() + 1) * sizeof(int));
+    VIE_CK(cudaMemcpyAsync(h, g->ost, sizeof(SegState), cudaMemcpyDeviceToHost, s));
+    VIE_CK(cudaEventRecord(g->ev[0], s));
+    VIE_TRY(wait_event(g->ev[0], timeout_ms));
+    *hs = *h;
+    return VIE_OK;
+}
+
+static int read_scalar(vie_grid* g, const double* d, double* out, cudaStream_t s, double timeout_ms) {
+    double* h = (double*)(g->h_ring + 2 * (g->groups.size() + 1) * sizeof(int) + sizeof(SegState));
+    VIE_CK(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CK(cudaEventRecord(g->ev[0], s));
+    VIE_TRY(wait_event(g->ev[0], timeout_ms));
+    *out = *h;
+    return VIE_OK;
+}
+
+struct SolveAccum {
+    int64_t inner_iters = 0;
+    int precond_applies = 0;
+    int mv128 = 0, mv64 = 0;
+};
+
+// Right-preconditioned BiCGSTAB on the full grid in precision C (Section II.B):
+// y = K2^{-1} p and z = K2^{-1} s each iteration, x updated with the y, z computed.
+template <class C>
+static int bicgstab_full(vie_grid* g, const vie_spectrum* sp, KrylovVecs<C> v, const vie_solve_opts* o,
+                         double tol, int maxit, cudaStream_t s, SolveAccum& acc, SegState* final_state) {
+    const bool pre = o->use_precond && g->nblocks > 0;
+    if (!pre) {
+        v.y = v.p;
+        v.z = v.s;
+    }
+    Bicg<C> k;
+    k.nseg = 1;
+    k.seglen = 3 * g->N;
+    k.v = v;
+    k.st = g->ost;
+    k.red = &g->ored;
+    VIE_TRY(bicg_init<C>(k, tol, maxit, s));
+    SegState hs;
+    VIE_TRY(read_outer_state(g, &hs, s, o->wait_timeout_ms));
+    vie_precond_stats ps;
+    auto precond = [&](const C* in, C* outv) -> int {
+        VIE_TRY(precond_apply<C>(g, sp, in, outv, o->inner_tol, o->inner_maxit, s, &ps, o->wait_timeout_ms));
+        acc.precond_applies++;
+        acc.inner_iters += (int64_t)std::llround(ps.mean_iters * ps.nblocks);
+        return VIE_OK;
+    };
+    for (int it = 0; it < maxit && hs.status == SEG_ACTIVE; ++it) {
+        VIE_TRY(bicg_rho<C>(k, s));
+        VIE_TRY(bicg_update_p<C>(k, s));
+        if (pre) VIE_TRY(precond(k.v.p, k.v.y));
+        VIE_TRY(mvm_full<C>(g, sp, k.v.y, k.v.v, s));
+        (prec_of<C>() == VIE_C128 ? acc.mv128 : acc.mv64)++;
+        VIE_TRY(bicg_sigma<C>(k, s));
+        VIE_TRY(bicg_update_s<C>(k, s));
+        VIE_TRY(bicg_x_half<C>(k, s));
+        VIE_TRY(read_outer_state(g, &hs, s, o->wait_timeout_ms));
+        if (hs.status != SEG_ACTIVE) break;
+        if (pre) VIE_TRY(precond(k.v.s, k.v.z));
+        VIE_TRY(mvm_full<C>(g, sp, k.v.z, k.v.t, s));
+        (prec_of<C>() == VIE_C128 ? acc.mv128 : acc.mv64)++;
+        VIE_TRY(bicg_omega<C>(k, s));
+        VIE_TRY(bicg_update_xr<C>(k, s));
+        VIE_TRY(read_outer_state(g, &hs, s, o->wait_timeout_ms));
+    }
+    VIE_TRY(read_outer_state(g, &hs, s, o->wait_timeout_ms));
+    *final_state = hs;
+    return VIE_OK;
+}
+
+static int status_code(int seg_status) {
+    switch (seg_status) {
+        case SEG_CONVERGED: return VIE_OK;
+        case SEG_MAXIT: return VIE_ENOTCONV;
+        case SEG_ACTIVE: return VIE_ENOTCONV;
+        default: return VIE_EBREAKDOWN;
+    }
+}
+
+// ||E_inc - A E|| / ||E_inc|| in FP64 (complex128 MVM); r128 receives the residual.
+static int true_residual(vie_grid* g, const vie_spectrum* sp, const double2* b, const double2* x, double2* r,
+                         double bnorm2, double* rel, cudaStream_t s, double timeout_ms, SolveAccum& acc) {
+    VIE_TRY(mvm_full<double2>(g, sp, x, g->tmp128, s));
+    acc.mv128++;
+    VIE_TRY(vec_residual128(b, g->tmp128, r, 3 * g->N, s));
+    VIE_TRY(vec_norm2_128(r, 3 * g->N, &g->ored, g->dscal + 1, s));
+    double rn2 = 0;
+    VIE_TRY(read_scalar(g, g->dscal + 1, &rn2, s, timeout_ms));
+    *rel = bnorm2 > 0 ? std::sqrt(rn2 / bnorm2) : 0.0;
+    return VIE_OK;
+}
+
+}  // namespace vie
+
+extern "C" int vie_plane_wave(const vie_grid* g, double k0, const double* khat, const double* pol, int precision,
+                              void* out, vie_stream_t stream) {
+    if (!g || !khat || !pol || !out) return fail(VIE_EINVAL, "vie_plane_wave: null argument");
+    if (precision != VIE_C128 && precision != VIE_C64) return fail(VIE_EINVAL, "vie_plane_wave: bad precision");
+    return plane_wave_launch(g, k0, khat, pol, precision, out, (cudaStream_t)stream);
+}
+
+extern "C" int vie_matvec(vie_grid* g, const vie_spectrum* sp, int precision, const void* x, void* y,
+                          vie_stream_t stream) {
+    if (!g || !x || !y) return fail(VIE_EINVAL, "vie_matvec: null argument");
+    VIE_TRY(check_spectrum(g, sp, precision));
+    const int64_t bytes = 3 * g->N * (precision == VIE_C128 ? 16 : 8);
+    if (overlaps(x, y, bytes)) return fail(VIE_EINVAL, "vie_matvec: x and y overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == VIE_C128) return mvm_full<double2>(g, sp, (const double2*)x, (double2*)y, s);
+    return mvm_full<float2>(g, sp, (const float2*)x, (float2*)y, s);
+}
+
+extern "C" int vie_block_precond_apply(vie_grid* g, const vie_spectrum* sp, int precision, const void* b, void* y,
+                                       double inner_tol, int inner_maxit, vie_stream_t stream,
+                                       vie_precond_stats* stats) {
+    if (!g || !b || !y) return fail(VIE_EINVAL, "vie_block_precond_apply: null argument");
+    VIE_TRY(check_spectrum(g, sp, precision));
+    if (!(inner_tol > 0.0) || inner_maxit < 1) return fail(VIE_EINVAL, "vie_block_precond_apply: bad tolerance or maxit");
+    const int64_t bytes = 3 * g->N * (precision == VIE_C128 ? 16 : 8);
+    if (overlaps(b, y, bytes)) return fail(VIE_EINVAL, "vie_block_precond_apply: b and y overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if (precision == VIE_C128)
+        rc = precond_apply<double2>(g, sp, (const double2*)b, (double2*)y, inner_tol, inner_maxit, s, stats, 0);
+    else
+        rc = precond_apply<float2>(g, sp, (const float2*)b, (float2*)y, inner_tol, inner_maxit, s, stats, 0);
+    if (rc) return rc;
+    VIE_CK(cudaEventRecord(g->ev[0], s));
+    return wait_event(g->ev[0], 0);
+}
+
+extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, void* e, const vie_solve_opts* o,
+                         vie_stream_t stream, vie_solve_stats* stats) {
+    if (!g || !einc || !e || !o) return fail(VIE_EINVAL, "vie_solve: null argument");
+    VIE_TRY(check_spectrum(g, sp, VIE_C128));
+    if (o->mode == VIE_MODE_MIXED) VIE_TRY(check_spectrum(g, sp, VIE_C64));
+    else if (o->mode != VIE_MODE_PLAIN_C128) return fail(VIE_EINVAL, "vie_solve: bad mode");
+    if (!(o->outer_tol > 0.0) || o->outer_maxit < 1) return fail(VIE_EINVAL, "vie_solve: bad outer tolerance or maxit");
+    if (o->use_precond && (!(o->inner_tol > 0.0) || o->inner_maxit < 1))
+        return fail(VIE_EINVAL, "vie_solve: bad inner tolerance or maxit");
+    const int64_t n3 = 3 * g->N;
+    if (overlaps(einc, e, n3 * 16)) return fail(VIE_EINVAL, "vie_solve: einc and e overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double tmo = o->wait_timeout_ms;
+    SolveAccum acc;
+    vie_solve_stats st;
+    memset(&st, 0, sizeof(st));
+    const double2* b = (const double2*)einc;
+    double2* x = (double2*)e;
+
+    VIE_TRY(vec_norm2_128(b, n3, &g->ored, g->dscal, s));
+    double bn2 = 0;
+    VIE_TRY(read_scalar(g, g->dscal, &bn2, s, tmo));
+    int rc = VIE_OK;
+    if (o->mode == VIE_MODE_PLAIN_C128) {
+        KrylovVecs<double2> v = g->o128;
+        v.b = const_cast<double2*>(b);
+        v.x = x;
+        SegState fs;
+        VIE_TRY(bicgstab_full<double2>(g, sp, v, o, o->outer_tol, o->outer_maxit, s, acc, &fs));
+        st.outer_iters = fs.iters;
+        rc = status_code(fs.status);
+        VIE_TRY(true_residual(g, sp, b, x, g->o128.r, bn2, &st.true_rel_res, s, tmo, acc));
+    } else {
+        // iterative refinement: FP64 residual, complex64 preconditioned correction
+        const int maxref = o->max_refinements > 0 ? o->max_refinements : 8;
+        VIE_CK(cudaMemsetAsync(x, 0, n3 * sizeof(double2), s));
+        VIE_TRY(vec_copy<double2>(b, g->o128.r, n3, s));
+        double rel = bn2 > 0 ? 1.0 : 0.0;
+        double rn2 = bn2;
+        VIE_CK(cudaMemcpyAsync(g->dscal + 1, g->dscal, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        rc = VIE_ENOTCONV;
+        for (int ref = 0; ref <= maxref; ++ref) {
+            if (ref > 0) {
+                VIE_TRY(true_residual(g, sp, b, x, g->o128.r, bn2, &rel, s, tmo, acc));
+                st.refinements++;
+            }
+            if (rel <= o->outer_tol) {
+                rc = VIE_OK;
+                break;
+            }
+            if (ref == maxref) break;
+            (void)rn2;
+            VIE_TRY(vec_scale_to_c64(g->o128.r, g->dscal + 1, g->o64.b, n3, s));
+            const double eta = std::max(0.5 * o->outer_tol / rel, 1e-4);
+            SegState fs;
+            VIE_TRY(bicgstab_full<float2>(g, sp, g->o64, o, std::min(eta, 0.5), o->outer_maxit, s, acc, &fs));
+            st.outer_iters += fs.iters;
+            if (fs.status == SEG_BREAKDOWN && fs.iters == 0) {
+                rc = VIE_EBREAKDOWN;
+                break;
+            }
+            VIE_TRY(vec_add_scaled_c64(x, g->o64.x, g->dscal + 1, n3, s));
+        }
+        st.true_rel_res = rel;
+    }
+    st.inner_iters = acc.inner_iters;
+    st.precond_applies = acc.precond_applies;
+    st.matvecs_c128 = acc.mv128;
+    st.matvecs_c64 = acc.mv64;
+    st.status = rc;
+    if (stats) *stats = st;
+    if (rc != VIE_OK) {
+        if (rc == VIE_ENOTCONV) set_error("vie_solve: iteration limit reached before the tolerance");
+        if (rc == VIE_EBREAKDOWN) set_error("vie_solve: BiCGSTAB breakdown");
+    }
+    return rc;
+}

@@ -1,0 +1,423 @@
+// Pencil FFT passes and the FFT-accelerated MVM y = x - G(chi x) (Section I;
+// Eq. 4 discretised on the voxel grid).
+//
+// Every 3D transform is split into three batched 1D passes. Forward passes are
+// radix-4 (plus one radix-2) decimation-in-frequency: natural order in,
+// bit-reversed order out. Inverse passes are decimation-in-time: bit-reversed
+// in, natural out. Intermediate spectra therefore live in bit-reversed
+// position order on every axis, and the Green spectrum is generated in the
+// same order, so no pass ever reorders data.
+//
+// One MVM over a batch of boxes (BoxSet; the full grid is the batch of one):
+//   pass X  rows of bx -> chi * x, zero-pad to Mx, forward   -> w1 [3][bz][by][Mx]
+//   pass Y  columns of by -> zero-pad to My, forward         -> w2 [3][bz][My][Mx]
+//   pass Z  columns of bz -> zero-pad to Mz, forward, 3x3 symmetric Green
+//           multiply, inverse, keep z < bz                   -> w2 (in place)
+//   pass Y' inverse, keep y < by                             -> w1
+//   pass X' inverse, keep x < bx, y = x - u (masked)         -> y
+// Each pass stages a tile of pencils in shared memory; global accesses are
+// along the contiguous x axis in every pass.
+#include "vie_internal.cuh"
+
+namespace vie {
+
+constexpr int kThreads = 256;
+constexpr int kSmemBudget = 64 * 1024;
+
+// ---------------------------------------------------------------- butterflies
+// Forward radix-4 DIF butterfly on (x0, x1, x2, x3) = positions (a, a+s, a+2s, a+3s)
+// of a group of 4s, with w_k = W_{4s}^{k j}; equals two radix-2 DIF stages.
+template <class C>
+__device__ __forceinline__ void bfly4_dif(C& x0, C& x1, C& x2, C& x3, C w1, C w2, C w3) {
+    C a0 = x0 + x2, a1 = x1 + x3, d0 = x0 - x2, d1 = mul_mi(x1 - x3);
+    x0 = a0 + a1;
+    x1 = cmul(a0 - a1, w2);
+    x2 = cmul(d0 + d1, w1);
+    x3 = cmul(d0 - d1, w3);
+}
+
+// Inverse of bfly4_dif up to a factor 4 (conjugate twiddles, DIT order).
+template <class C>
+__device__ __forceinline__ void bfly4_dit(C& x0, C& x1, C& x2, C& x3, C w1, C w2, C w3) {
+    C p = x0, q = cmulc(x1, w2), u = cmulc(x2, w1), v = cmulc(x3, w3);
+    C pq = p + q, pmq = p - q, uv = u + v, iumv = mul_i(u - v);
+    x0 = pq + uv;
+    x2 = pq - uv;
+    x1 = pmq + iumv;
+    x3 = pmq - iumv;
+}
+
+// In-place FFT of NCOMP * (1 << ltc) columns of length L = 1 << lL held in
+// shared memory: element (i, comp, c) at buf[i * pitch + comp * (1 << ltc) + c].
+// FWD: natural -> bit-reversed (DIF). !FWD: bit-reversed -> natural (DIT),
+// unnormalised (L times the inverse DFT). Ends with __syncthreads().
+template <class C, bool FWD, int NCOMP>
+__device__ void smem_fft(C* buf, int lL, int pitch, int ltc, const C* __restrict__ tw, int twshift) {
+    const int tcm = (1 << ltc) - 1;
+    const int nq = ((1 << lL) >> 2) * NCOMP << ltc;   // radix-4 butterflies per stage
+    const int nr4 = lL >> 1;
+    const bool odd = lL & 1;
+    auto radix2 = [&]() {
+        const int n2 = ((1 << lL) >> 1) * NCOMP << ltc;
+        for (int idx = threadIdx.x; idx < n2; idx += blockDim.x) {
+            int c = idx & tcm, t = idx >> ltc;
+            int comp = t % NCOMP, q = t / NCOMP;
+            C* p0 = buf + (2 * q) * pitch + (comp << ltc) + c;
+            C x0 = p0[0], x1 = p0[pitch];
+            p0[0] = x0 + x1;
+            p0[pitch] = x0 - x1;
+        }
+        __syncthreads();
+    };
+    if (!FWD && odd) radix2();
+    for (int st = 0; st < nr4; ++st) {
+        const int ls = FWD ? (lL - 2 - 2 * st) : ((odd ? 1 : 0) + 2 * st);   // log2 of span s
+        const int sm = (1 << ls) - 1;
+        const int sp = pitch << ls;
+        for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+            int c = idx & tcm, t = idx >> ltc;
+            int comp = t % NCOMP, q = t / NCOMP;
+            int j = q & sm, g = q >> ls;
+            int a0 = (g << (ls + 2)) + j;
+            int e = j << (lL - ls - 2);                  // j * L / (4 s)
+            C w1 = tw[e << twshift], w2 = tw[(2 * e) << twshift], w3 = tw[(3 * e) << twshift];
+            C* p0 = buf + a0 * pitch + (comp << ltc) + c;
+            C x0 = p0[0], x1 = p0[sp], x2 = p0[2 * sp], x3 = p0[3 * sp];
+            if (FWD) bfly4_dif(x0, x1, x2, x3, w1, w2, w3);
+            else bfly4_dit(x0, x1, x2, x3, w1, w2, w3);
+            p0[0] = x0;
+            p0[sp] = x1;
+            p0[2 * sp] = x2;
+            p0[3 * sp] = x3;
+        }
+        __syncthreads();
+    }
+    if (FWD && odd) radix2();
+}
+
+__device__ __forceinline__ bool box_active(const SegState* st, int b) {
+    return st == nullptr || st[b].status == SEG_ACTIVE;
+}
+
+// ---------------------------------------------------------------- pass X (rows)
+enum RowMode { ROW_FWD_CHI = 0, ROW_INV_UPDATE = 1, ROW_FWD_PLAIN = 2 };
+
+template <class C> struct RowArgs {
+    const C* in;
+    C* out;
+    const C* chi;        // ROW_FWD_CHI: [nb][bz][by][bx]
+    const C* xin;        // ROW_INV_UPDATE: x, same layout as out
+    const uint8_t* mask; // ROW_INV_UPDATE: optional [nb][bz][by][bx]
+    const SegState* st;  // optional per-box status
+    const C* tw;
+    int64_t nrows;
+    int in_stride, out_stride, n_in, n_out, lL, ltr, twshift;
+    int rows_per_box;    // 3 * bz * by
+    int plane;           // bz * by
+    int bx;
+};
+
+template <class C, int MODE>
+__global__ void __launch_bounds__(kThreads) k_rows(RowArgs<C> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int TR = 1 << a.ltr;
+    const int pitch = TR + 1;          // odd pitch: conflict-free transposed staging
+    const int L = 1 << a.lL;
+    const int64_t row0 = (int64_t)blockIdx.x * TR;
+
+    for (int idx = threadIdx.x; idx < TR * a.n_in; idx += blockDim.x) {
+        int r = idx / a.n_in, i = idx - r * a.n_in;
+        int64_t row = row0 + r;
+        C v = czero<C>();
+        if (row < a.nrows) {
+            int b = (int)(row / a.rows_per_box);
+            if (box_active(a.st, b)) {
+                v = a.in[row * a.in_stride + i];
+                if (MODE == ROW_FWD_CHI) {
+                    int64_t crow = (int64_t)b * a.plane + (row % a.plane);
+                    v = cmul(v, a.chi[crow * a.bx + i]);
+                }
+            }
+        }
+        buf[i * pitch + r] = v;
+    }
+    for (int idx = threadIdx.x; idx < TR * (L - a.n_in); idx += blockDim.x) {
+        int i = a.n_in + idx / TR, r = idx % TR;
+        buf[i * pitch + r] = czero<C>();
+    }
+    __syncthreads();
+    smem_fft<C, MODE != ROW_INV_UPDATE, 1>(buf, a.lL, pitch, a.ltr, a.tw, a.twshift);
+    for (int idx = threadIdx.x; idx < TR * a.n_out; idx += blockDim.x) {
+        int r = idx / a.n_out, i = idx - r * a.n_out;
+        int64_t row = row0 + r;
+        if (row >= a.nrows) continue;
+        int b = (int)(row / a.rows_per_box);
+        if (!box_active(a.st, b)) continue;
+        C v = buf[i * pitch + r];
+        if (MODE == ROW_INV_UPDATE) {
+            int64_t o = row * a.out_stride + i;
+            v = a.xin[o] - v;
+            if (a.mask != nullptr) {
+                int64_t mrow = (int64_t)b * a.plane + (row % a.plane);
+                if (!a.mask[mrow * a.bx + i]) v = czero<C>();
+            }
+            a.out[o] = v;
+        } else {
+            a.out[row * a.out_stride + i] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- pass Y / spectrum passes (columns)
+template <class C> struct ColArgs {
+    const C* in;
+    C* out;
+    const SegState* st;
+    const C* tw;
+    int ncols, n_in, n_out, lL, ltc, twshift;
+    int64_t in_axis, out_axis, in_s1, out_s1, in_s2, out_s2;
+    int b2_per_box;      // blockIdx.z / b2_per_box = box index
+};
+
+template <class C, bool FWD>
+__global__ void __launch_bounds__(kThreads) k_cols(ColArgs<C> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int TC = 1 << a.ltc;
+    const int L = 1 << a.lL;
+    const int col0 = blockIdx.x * TC;
+    if (!box_active(a.st, blockIdx.z / a.b2_per_box)) return;   // uniform per CTA
+    const C* in = a.in + blockIdx.z * a.in_s2 + blockIdx.y * a.in_s1 + col0;
+    C* out = a.out + blockIdx.z * a.out_s2 + blockIdx.y * a.out_s1 + col0;
+    const int ncol = min(TC, a.ncols - col0);
+
+    for (int idx = threadIdx.x; idx < L * TC; idx += blockDim.x) {
+        int i = idx >> a.ltc, c = idx & (TC - 1);
+        C v = czero<C>();
+        if (i < a.n_in && c < ncol) v = in[i * a.in_axis + c];
+        buf[idx] = v;
+    }
+    __syncthreads();
+    smem_fft<C, FWD, 1>(buf, a.lL, TC, a.ltc, a.tw, a.twshift);
+    for (int idx = threadIdx.x; idx < a.n_out * TC; idx += blockDim.x) {
+        int i = idx >> a.ltc, c = idx & (TC - 1);
+        if (c < ncol) out[i * a.out_axis + c] = buf[idx];
+    }
+}
+
+// ---------------------------------------------------------------- pass Z fused with the Green multiply
+template <class C> struct ZArgs {
+    C* w;                 // w2 of the BoxSet
+    const C* G;           // [6][Mz][My][Mx]
+    const SegState* st;
+    const C* tw;
+    int ncols, nzb, lL, ltc, twshift;
+    int64_t axis, comp_stride, box_stride, gcomp;
+};
+
+template <class C>
+__global__ void __launch_bounds__(kThreads) k_zgreen(ZArgs<C> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int TC = 1 << a.ltc;
+    const int L = 1 << a.lL;
+    const int pitch = 3 * TC;
+    const int col0 = blockIdx.x * TC;
+    const int b = blockIdx.y;
+    if (!box_active(a.st, b)) return;
+    C* w = a.w + b * a.box_stride + col0;
+    const int ncol = min(TC, a.ncols - col0);
+
+    for (int idx = threadIdx.x; idx < L * 3 * TC; idx += blockDim.x) {
+        int c = idx & (TC - 1), t = idx >> a.ltc;
+        int comp = t % 3, i = t / 3;
+        C v = czero<C>();
+        if (i < a.nzb && c < ncol) v = w[comp * a.comp_stride + i * a.axis + c];
+        buf[idx] = v;     // idx == i * pitch + comp * TC + c
+    }
+    __syncthreads();
+    smem_fft<C, true, 3>(buf, a.lL, pitch, a.ltc, a.tw, a.twshift);
+    for (int idx = threadIdx.x; idx < L * TC; idx += blockDim.x) {
+        int c = idx & (TC - 1), i = idx >> a.ltc;
+        if (c >= ncol) continue;
+        const C* g = a.G + i * a.axis + col0 + c;
+        C gxx = g[0], gxy = g[a.gcomp], gxz = g[2 * a.gcomp];
+        C gyy = g[3 * a.gcomp], gyz = g[4 * a.gcomp], gzz = g[5 * a.gcomp];
+        C* p = buf + i * pitch + c;
+        C X = p[0], Y = p[TC], Z = p[2 * TC];
+        p[0] = cmul(gxx, X) + cmul(gxy, Y) + cmul(gxz, Z);
+        p[TC] = cmul(gxy, X) + cmul(gyy, Y) + cmul(gyz, Z);
+        p[2 * TC] = cmul(gxz, X) + cmul(gyz, Y) + cmul(gzz, Z);
+    }
+    __syncthreads();
+    smem_fft<C, false, 3>(buf, a.lL, pitch, a.ltc, a.tw, a.twshift);
+    for (int idx = threadIdx.x; idx < a.nzb * 3 * TC; idx += blockDim.x) {
+        int c = idx & (TC - 1), t = idx >> a.ltc;
+        int comp = t % 3, i = t / 3;
+        if (c < ncol) w[comp * a.comp_stride + i * a.axis + c] = buf[idx];
+    }
+}
+
+// ---------------------------------------------------------------- host side
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// log2 of the pencils per CTA: as many as fit the shared-memory budget, at most 32.
+static int pick_ltile(int lL, size_t esize, int ncomp, int pad) {
+    int lt = 5;
+    while (lt > 0 && (size_t)((1 << lL)) * (size_t)(ncomp * (1 << lt) + pad) * esize > (size_t)kSmemBudget) --lt;
+    return lt;
+}
+
+template <class C> static const C* tw_ptr(const Twiddles& t);
+template <> const double2* tw_ptr<double2>(const Twiddles& t) { return t.d128; }
+template <> const float2* tw_ptr<float2>(const Twiddles& t) { return t.d64; }
+
+template <class K>
+static int prep_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+    }
+    return VIE_OK;
+}
+
+template <class C, int MODE>
+static int launch_rows(RowArgs<C> a, cudaStream_t s) {
+    a.ltr = pick_ltile(a.lL, sizeof(C), 1, 1);
+    const int TR = 1 << a.ltr;
+    size_t smem = (size_t)(1 << a.lL) * (TR + 1) * sizeof(C);
+    VIE_TRY(prep_smem(k_rows<C, MODE>, smem));
+    int64_t grid = (a.nrows + TR - 1) / TR;
+    if (grid <= 0) return VIE_OK;
+    k_rows<C, MODE><<<(unsigned)grid, kThreads, smem, s>>>(a);
+    VIE_CK(cudaGetLastError());
+    return VIE_OK;
+}
+
+template <class C, bool FWD>
+static int launch_cols(ColArgs<C> a, int nb1, int nb2, cudaStream_t s) {
+    a.ltc = pick_ltile(a.lL, sizeof(C), 1, 0);
+    if ((1 << a.ltc) > a.ncols) a.ltc = ilog2(a.ncols) - ((1 << ilog2(a.ncols)) > a.ncols ? 1 : 0);
+    if (a.ltc < 0) a.ltc = 0;
+    const int TC = 1 << a.ltc;
+    size_t smem = (size_t)(1 << a.lL) * TC * sizeof(C);
+    VIE_TRY(prep_smem(k_cols<C, FWD>, smem));
+    dim3 grid((a.ncols + TC - 1) / TC, nb1, nb2);
+    k_cols<C, FWD><<<grid, kThreads, smem, s>>>(a);
+    VIE_CK(cudaGetLastError());
+    return VIE_OK;
+}
+
+template <class C>
+static int launch_zgreen(ZArgs<C> a, int nb, cudaStream_t s) {
+    a.ltc = pick_ltile(a.lL, sizeof(C), 3, 0);
+    if ((1 << a.ltc) > a.ncols) a.ltc = ilog2(a.ncols) - ((1 << ilog2(a.ncols)) > a.ncols ? 1 : 0);
+    if (a.ltc < 0) a.ltc = 0;
+    const int TC = 1 << a.ltc;
+    size_t smem = (size_t)(1 << a.lL) * 3 * TC * sizeof(C);
+    VIE_TRY(prep_smem(k_zgreen<C>, smem));
+    dim3 grid((a.ncols + TC - 1) / TC, nb);
+    k_zgreen<C><<<grid, kThreads, smem, s>>>(a);
+    VIE_CK(cudaGetLastError());
+    return VIE_OK;
+}
+
+template <class C> static const C* chi_ptr(const BoxSet& bs);
+template <> const double2* chi_ptr<double2>(const BoxSet& bs) { return bs.chi128; }
+template <> const float2* chi_ptr<float2>(const BoxSet& bs) { return bs.chi64; }
+
+template <class C>
+int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st, cudaStream_t s) {
+    Twiddles tw;
+    VIE_TRY(get_twiddles(&tw));
+    const C* T = tw_ptr<C>(tw);
+    C* w1 = reinterpret_cast<C*>(bs.w1);
+    C* w2 = reinterpret_cast<C*>(bs.w2);
+    const int64_t planeXY = (int64_t)bs.Mx * bs.My;
+
+    // pass X: chi * x, zero-padded forward FFT of every row
+    RowArgs<C> rx{};
+    rx.in = x; rx.out = w1; rx.chi = chi_ptr<C>(bs); rx.st = st; rx.tw = T;
+    rx.nrows = (int64_t)bs.nb * 3 * bs.bz * bs.by;
+    rx.in_stride = bs.bx; rx.out_stride = bs.Mx; rx.n_in = bs.bx; rx.n_out = bs.Mx;
+    rx.lL = bs.lx; rx.twshift = kLogLmax - bs.lx;
+    rx.rows_per_box = 3 * bs.bz * bs.by; rx.plane = bs.bz * bs.by; rx.bx = bs.bx;
+    VIE_TRY((launch_rows<C, ROW_FWD_CHI>(rx, s)));
+
+    // pass Y forward
+    ColArgs<C> cy{};
+    cy.in = w1; cy.out = w2; cy.st = st; cy.tw = T;
+    cy.ncols = bs.Mx; cy.n_in = bs.by; cy.n_out = bs.My; cy.lL = bs.ly; cy.twshift = kLogLmax - bs.ly;
+    cy.in_axis = bs.Mx; cy.out_axis = bs.Mx;
+    cy.in_s1 = (int64_t)bs.by * bs.Mx; cy.out_s1 = planeXY;
+    cy.in_s2 = (int64_t)bs.bz * bs.by * bs.Mx; cy.out_s2 = (int64_t)bs.bz * planeXY;
+    cy.b2_per_box = 3;
+    VIE_TRY((launch_cols<C, true>(cy, bs.bz, bs.nb * 3, s)));
+
+    // pass Z: forward, Green multiply, inverse
+    ZArgs<C> z{};
+    z.w = w2; z.G = G; z.st = st; z.tw = T;
+    z.ncols = (int)planeXY; z.nzb = bs.bz; z.lL = bs.lz; z.twshift = kLogLmax - bs.lz;
+    z.axis = planeXY; z.comp_stride = (int64_t)bs.bz * planeXY; z.box_stride = 3 * z.comp_stride;
+    z.gcomp = (int64_t)bs.Mz * planeXY;
+    VIE_TRY(launch_zgreen<C>(z, bs.nb, s));
+
+    // pass Y inverse: keep y < by
+    ColArgs<C> iy = cy;
+    iy.in = w2; iy.out = w1; iy.n_in = bs.My; iy.n_out = bs.by;
+    iy.in_s1 = planeXY; iy.out_s1 = (int64_t)bs.by * bs.Mx;
+    iy.in_s2 = (int64_t)bs.bz * planeXY; iy.out_s2 = (int64_t)bs.bz * bs.by * bs.Mx;
+    VIE_TRY((launch_cols<C, false>(iy, bs.bz, bs.nb * 3, s)));
+
+    // pass X inverse: keep x < bx, y = x - u
+    RowArgs<C> ix = rx;
+    ix.in = w1; ix.out = y; ix.xin = x; ix.mask = bs.mask; ix.chi = nullptr;
+    ix.in_stride = bs.Mx; ix.out_stride = bs.bx; ix.n_in = bs.Mx; ix.n_out = bs.bx;
+    VIE_TRY((launch_rows<C, ROW_INV_UPDATE>(ix, s)));
+    return VIE_OK;
+}
+
+template <class C>
+int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s) {
+    Twiddles tw;
+    VIE_TRY(get_twiddles(&tw));
+    const C* T = tw_ptr<C>(tw);
+    const int64_t planeXY = (int64_t)bs.Mx * bs.My;
+    const int64_t vol = planeXY * bs.Mz;
+
+    RowArgs<C> rx{};
+    rx.in = G; rx.out = G; rx.tw = T;
+    rx.nrows = 6 * (int64_t)bs.Mz * bs.My;
+    rx.in_stride = bs.Mx; rx.out_stride = bs.Mx; rx.n_in = bs.Mx; rx.n_out = bs.Mx;
+    rx.lL = bs.lx; rx.twshift = kLogLmax - bs.lx;
+    rx.rows_per_box = (int)std::min<int64_t>(rx.nrows, 1 << 30); rx.plane = 1; rx.bx = bs.Mx;
+    VIE_TRY((launch_rows<C, ROW_FWD_PLAIN>(rx, s)));
+
+    ColArgs<C> cy{};
+    cy.in = G; cy.out = G; cy.tw = T; cy.b2_per_box = 1;
+    cy.ncols = bs.Mx; cy.n_in = bs.My; cy.n_out = bs.My; cy.lL = bs.ly; cy.twshift = kLogLmax - bs.ly;
+    cy.in_axis = cy.out_axis = bs.Mx;
+    cy.in_s1 = cy.out_s1 = planeXY;
+    cy.in_s2 = cy.out_s2 = vol;
+    VIE_TRY((launch_cols<C, true>(cy, bs.Mz, 6, s)));
+
+    ColArgs<C> cz{};
+    cz.in = G; cz.out = G; cz.tw = T; cz.b2_per_box = 1;
+    cz.ncols = (int)planeXY; cz.n_in = bs.Mz; cz.n_out = bs.Mz; cz.lL = bs.lz; cz.twshift = kLogLmax - bs.lz;
+    cz.in_axis = cz.out_axis = planeXY;
+    cz.in_s1 = cz.out_s1 = 0;
+    cz.in_s2 = cz.out_s2 = vol;
+    VIE_TRY((launch_cols<C, true>(cz, 1, 6, s)));
+    return VIE_OK;
+}
+
+template int mvm_boxes<double2>(const BoxSet&, const double2*, const double2*, double2*, const SegState*, cudaStream_t);
+template int mvm_boxes<float2>(const BoxSet&, const float2*, const float2*, float2*, const SegState*, cudaStream_t);
+template int spectrum_fft<double2>(const BoxSet&, double2*, cudaStream_t);
+
+}  // namespace vie

@@ -1,0 +1,219 @@
+// Internal declarations of libvie: complex helpers, handle layouts, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vie.h"
+
+namespace vie {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define VIE_CK(call)                                                        \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return ::vie::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define VIE_TRY(call)                                                       \
+    do {                                                                    \
+        int rc_ = (call);                                                   \
+        if (rc_ != VIE_OK) return rc_;                                      \
+    } while (0)
+
+// ---------------------------------------------------------------- complex
+template <class C> struct real_of;
+template <> struct real_of<double2> { typedef double type; };
+template <> struct real_of<float2> { typedef float type; };
+
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+template <class C> __host__ __device__ __forceinline__ C cmk(double a, double b);
+template <> __host__ __device__ __forceinline__ double2 cmk<double2>(double a, double b) { return make_double2(a, b); }
+template <> __host__ __device__ __forceinline__ float2 cmk<float2>(double a, double b) { return make_float2((float)a, (float)b); }
+
+#define VIE_CPLX_OPS(C)                                                                   \
+    __host__ __device__ __forceinline__ C operator+(C a, C b) { return mk(a.x + b.x, a.y + b.y); } \
+    __host__ __device__ __forceinline__ C operator-(C a, C b) { return mk(a.x - b.x, a.y - b.y); } \
+    __host__ __device__ __forceinline__ C cmul(C a, C b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); } \
+    __host__ __device__ __forceinline__ C cmulc(C a, C b) { /* a * conj(b) */ return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); } \
+    __host__ __device__ __forceinline__ C mul_i(C a) { return mk(-a.y, a.x); }          \
+    __host__ __device__ __forceinline__ C mul_mi(C a) { return mk(a.y, -a.x); }
+
+VIE_CPLX_OPS(double2)
+VIE_CPLX_OPS(float2)
+#undef VIE_CPLX_OPS
+
+template <class C> __host__ __device__ __forceinline__ C czero() { return cmk<C>(0.0, 0.0); }
+
+__device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+__device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
+template <class C> __device__ __forceinline__ C from_c128(double2 a);
+template <> __device__ __forceinline__ double2 from_c128<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_c128<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// ---------------------------------------------------------------- FFT plan pieces
+constexpr int kLmax = 1024;   // largest padded FFT length per axis
+constexpr int kLogLmax = 10;
+
+struct Twiddles {              // W_Lmax^m = exp(-2 pi i m / Lmax), m in [0, Lmax)
+    double2* d128 = nullptr;
+    float2* d64 = nullptr;
+};
+int get_twiddles(Twiddles* out);   // per device, created on first use
+
+// A batch of equal-shaped boxes sharing one padded FFT shape. The full-grid
+// operator is the batch with nb = 1 and the box equal to the grid.
+struct BoxSet {
+    int nb = 0;
+    int bx = 0, by = 0, bz = 0;        // box dimensions (voxels)
+    int Mx = 0, My = 0, Mz = 0;        // padded FFT lengths (powers of two >= 2b - 1)
+    int lx = 0, ly = 0, lz = 0;        // log2 of the padded lengths
+    double2* chi128 = nullptr;         // [nb][bz][by][bx], chi masked to each block
+    float2* chi64 = nullptr;
+    uint8_t* mask = nullptr;           // [nb][bz][by][bx] block membership, or null (full grid)
+    int32_t* origin = nullptr;         // [nb][3] grid coordinates of each box corner
+    void* w1 = nullptr;                // [nb][3][bz][by][Mx] (sized for complex128)
+    void* w2 = nullptr;                // [nb][3][bz][My][Mx]
+    std::vector<int> block_ids;        // compact block index of each box
+
+    int64_t box_elems() const { return (int64_t)bx * by * bz; }
+    int64_t vec_elems() const { return 3 * box_elems(); }             // per box
+    int64_t spec_elems() const { return (int64_t)Mx * My * Mz; }      // per component
+};
+
+// Per-segment BiCGSTAB state (FP64 scalars on the device).
+enum SegStatus : int {
+    SEG_ACTIVE = 0,
+    SEG_CONVERGED = 1,
+    SEG_HALF_PENDING = 2,  // converged at the half step, x += alpha y not applied yet
+    SEG_MAXIT = 3,
+    SEG_BREAKDOWN = 4,
+    SEG_IDLE = 5           // not part of this solve
+};
+
+struct SegState {
+    double2 rho, rho_prev, alpha, omega;
+    double bnorm2, res2, tol2;
+    double iters;          // half-steps counted as 0.5
+    int status;
+    int maxit;
+};
+
+// Batched Krylov workspace for one BoxSet (inner solves) or the full grid.
+template <class C> struct KrylovVecs {
+    C *b = nullptr, *x = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr,
+      *v = nullptr, *s = nullptr, *t = nullptr, *y = nullptr, *z = nullptr;
+};
+
+struct ReduceScratch {
+    double2* part = nullptr;     // [nseg][kMaxCtaPerSeg][2]
+    unsigned* count = nullptr;   // [nseg]
+    int* n_active = nullptr;     // [1]
+    int nseg = 0;
+};
+constexpr int kMaxCtaPerSeg = 256;
+
+struct Group {
+    BoxSet bs;
+    KrylovVecs<double2> k128;
+    KrylovVecs<float2> k64;
+    SegState* st = nullptr;            // [nb]
+    ReduceScratch red;
+};
+
+}  // namespace vie
+
+struct vie_spectrum {
+    vie_grid* grid = nullptr;
+    double k0 = 0.0;
+    int precision_mask = 0;
+    // index 0: full grid; 1 + g: group g. Layout [6][Mz][My][Mx] (bit-reversed
+    // frequency positions per axis), scaled by 1/(Mx My Mz).
+    std::vector<double2*> g128;
+    std::vector<float2*> g64;
+};
+
+struct vie_grid {
+    int device = 0;
+    int nx = 0, ny = 0, nz = 0;
+    double h = 0.0;
+    int64_t N = 0;
+    vie::BoxSet full;
+    int32_t* block_id = nullptr;          // device [N], compact ids, -1 = none
+    int nblocks = 0;
+    std::vector<vie::Group> groups;
+    int32_t* blk_group = nullptr;         // device [nblocks]
+    int32_t* blk_index = nullptr;         // device [nblocks]
+    int32_t* blk_origin = nullptr;        // device [nblocks][3]
+    // outer Krylov vectors (full grid)
+    vie::KrylovVecs<double2> o128;
+    vie::KrylovVecs<float2> o64;
+    double2* tmp128 = nullptr;            // full-grid scratch vector
+    float2* tmp64 = nullptr;
+    vie::SegState* ost = nullptr;         // outer state [1]
+    vie::ReduceScratch ored;
+    double* dscal = nullptr;              // device scalars: [0] ||b||^2, [1] ||r||^2
+    char* h_ring = nullptr;               // pinned host: active counts, state, scalar
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int64_t device_bytes = 0;
+    std::vector<void*> allocations;
+};
+
+namespace vie {
+
+// ---------------------------------------------------------------- launchers (fft.cu)
+template <class C>
+int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st,
+              cudaStream_t s);
+template <class C>
+int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s);   // in place, 6 components
+
+// ---------------------------------------------------------------- green.cu
+int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t s);
+int convert_c128_to_c64(const double2* a, float2* b, int64_t n, cudaStream_t s);
+int plane_wave_launch(const vie_grid* g, double k0, const double* khat, const double* pol,
+                      int precision, void* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- krylov.cu
+template <class C>
+struct Bicg {
+    int nseg;
+    int64_t seglen;
+    KrylovVecs<C> v;
+    SegState* st;
+    ReduceScratch* red;
+};
+template <class C> int bicg_init(Bicg<C>& k, double tol, int maxit, cudaStream_t s);
+template <class C> int bicg_rho(Bicg<C>& k, cudaStream_t s);
+template <class C> int bicg_update_p(Bicg<C>& k, cudaStream_t s);
+template <class C> int bicg_sigma(Bicg<C>& k, cudaStream_t s);
+template <class C> int bicg_update_s(Bicg<C>& k, cudaStream_t s);
+template <class C> int bicg_x_half(Bicg<C>& k, cudaStream_t s);
+template <class C> int bicg_omega(Bicg<C>& k, cudaStream_t s);
+template <class C> int bicg_update_xr(Bicg<C>& k, cudaStream_t s);
+int reduce_count_active(const SegState* st, int nseg, int* n_active, cudaStream_t s);
+
+// vector helpers (krylov.cu)
+template <class C> int vec_copy(const C* a, C* b, int64_t n, cudaStream_t s);
+int vec_residual128(const double2* b, const double2* ax, double2* r, int64_t n, cudaStream_t s);
+int vec_norm2_128(const double2* a, int64_t n, ReduceScratch* red, double* d_out, cudaStream_t s);
+int vec_scale_to_c64(const double2* a, const double* d_norm2, float2* b, int64_t n, cudaStream_t s);
+int vec_add_scaled_c64(double2* x, const float2* d, const double* d_norm2, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------- precond.cu
+template <class C>
+int precond_gather(const vie_grid* g, const Group& gr, const C* b, C* out, cudaStream_t s);
+template <class C>
+int precond_scatter_group(const vie_grid* g, const Group& gr, const C* xk, C* y, cudaStream_t s);
+template <class C>
+int precond_copy_unblocked(const vie_grid* g, const C* b, C* y, cudaStream_t s);
+
+}  // namespace vie

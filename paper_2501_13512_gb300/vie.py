@@ -1,0 +1,240 @@
+"""Python binding of libvie (include/vie.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch provides device memory
+and the current stream. Vectors are torch tensors of shape (3, nz, ny, nx),
+complex128 (VIE_C128) or complex64 (VIE_C64), contiguous, on the grid's GPU.
+If libvie.so is missing this module raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, byref, c_double, c_int, c_int32, c_int64, c_size_t, c_uint32, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvie.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "vie.h")
+
+VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA, VIE_ENOTCONV, VIE_EBREAKDOWN, VIE_ETIMEOUT, VIE_EBUSY = range(8)
+STATUS_NAMES = {0: "VIE_OK", 1: "VIE_EINVAL", 2: "VIE_ENOMEM", 3: "VIE_ECUDA", 4: "VIE_ENOTCONV",
+                5: "VIE_EBREAKDOWN", 6: "VIE_ETIMEOUT", 7: "VIE_EBUSY"}
+C128, C64 = 1, 2
+MODE_PLAIN_C128, MODE_MIXED = 0, 1
+
+
+class VieError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("h", c_double),
+                ("eps_r", POINTER(c_double)), ("block_id", POINTER(c_int32)), ("flags", c_uint32)]
+
+
+class GridInfo(ctypes.Structure):
+    _fields_ = [("nblocks", c_int32), ("ngroups", c_int32), ("Mx", c_int32), ("My", c_int32),
+                ("Mz", c_int32), ("device_bytes", c_int64)]
+
+
+class PrecondStats(ctypes.Structure):
+    _fields_ = [("nblocks", c_int32), ("max_iters", c_int32), ("mean_iters", c_double),
+                ("not_converged", c_int32), ("breakdowns", c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("outer_tol", c_double), ("inner_tol", c_double), ("outer_maxit", c_int32),
+                ("inner_maxit", c_int32), ("use_precond", c_int32), ("mode", c_int32),
+                ("max_refinements", c_int32), ("wait_timeout_ms", c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("outer_iters", c_double), ("inner_iters", c_int64), ("precond_applies", c_int32),
+                ("matvecs_c128", c_int32), ("matvecs_c64", c_int32), ("refinements", c_int32),
+                ("true_rel_res", c_double), ("status", c_int32)]
+
+
+def _struct_dict(s):
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+_lib = None
+
+
+def declared_functions(header=HEADER):
+    """Names of the entry points declared in include/vie.h."""
+    text = open(header).read()
+    return sorted(set(re.findall(r"^\s*int\s+(vie_\w+)\s*\(", text, re.M)))
+
+
+def load(path=LIB_PATH):
+    """Load libvie.so (built by paper_2501_13512_gb300.build) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libvie.so not found at {path}: run paper_2501_13512_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "vie_version": ([], c_int),
+        "vie_last_error": ([ctypes.c_char_p, c_size_t], c_int),
+        "vie_grid_create": ([POINTER(GridDesc), POINTER(P)], c_int),
+        "vie_grid_destroy": ([P], c_int),
+        "vie_grid_get_info": ([P, POINTER(GridInfo)], c_int),
+        "vie_green_spectrum": ([P, c_double, c_int, P, POINTER(P)], c_int),
+        "vie_spectrum_release": ([P], c_int),
+        "vie_plane_wave": ([P, c_double, POINTER(c_double), POINTER(c_double), c_int, P, P], c_int),
+        "vie_matvec": ([P, P, c_int, P, P, P], c_int),
+        "vie_block_precond_apply": ([P, P, c_int, P, P, c_double, c_int, P, POINTER(PrecondStats)], c_int),
+        "vie_solve": ([P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def last_error():
+    lib = load()
+    buf = ctypes.create_string_buffer(1024)
+    lib.vie_last_error(buf, 1024)
+    return buf.value.decode()
+
+
+def _check(rc, allow=()):
+    if rc != VIE_OK and rc not in allow:
+        raise VieError(rc, last_error())
+    return rc
+
+
+def _stream():
+    import torch
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype(precision):
+    import torch
+    return torch.complex128 if precision == C128 else torch.complex64
+
+
+class Spectrum:
+    def __init__(self, grid, handle, k0, mask):
+        self.grid = grid
+        self.handle = handle
+        self.k0 = k0
+        self.mask = mask
+
+    def release(self):
+        if self.handle:
+            _check(load().vie_spectrum_release(self.handle))
+            self.handle = None
+
+
+class Grid:
+    """A voxel grid with its contrast and block partition (vie_grid)."""
+
+    def __init__(self, eps_r, h, block_id=None):
+        lib = load()
+        eps_r = np.ascontiguousarray(eps_r, dtype=np.complex128)
+        nz, ny, nx = eps_r.shape
+        self.shape = (nz, ny, nx)
+        self.n = (nx, ny, nz)
+        self.h = float(h)
+        self._eps = eps_r.view(np.float64).reshape(-1)
+        self._bid = None if block_id is None else np.ascontiguousarray(block_id, dtype=np.int32).reshape(-1)
+        d = GridDesc(nx, ny, nz, self.h, self._eps.ctypes.data_as(POINTER(c_double)),
+                     None if self._bid is None else self._bid.ctypes.data_as(POINTER(c_int32)), 0)
+        handle = c_void_p()
+        _check(lib.vie_grid_create(byref(d), byref(handle)))
+        self.handle = handle
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w.eps_r, w.h, w.block_id if w.use_precond else None)
+
+    def info(self):
+        inf = GridInfo()
+        _check(load().vie_grid_get_info(self.handle, byref(inf)))
+        return _struct_dict(inf)
+
+    def close(self):
+        if self.handle:
+            _check(load().vie_grid_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, t, precision, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != _dtype(precision) or tuple(t.shape) != (3,) + self.shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {_dtype(precision)} tensor of shape {(3,) + self.shape}")
+        return c_void_p(t.data_ptr())
+
+    def empty(self, precision=C128):
+        import torch
+        return torch.empty((3,) + self.shape, dtype=_dtype(precision), device="cuda")
+
+    def spectrum(self, k0, precision=C128 | C64):
+        h = c_void_p()
+        _check(load().vie_green_spectrum(self.handle, float(k0), int(precision), _stream(), byref(h)))
+        return Spectrum(self, h, float(k0), precision)
+
+    def plane_wave(self, k0, khat, pol, precision=C128, out=None):
+        out = self.empty(precision) if out is None else out
+        kh = (c_double * 3)(*[float(v) for v in khat])
+        p = np.asarray(pol, dtype=np.complex128)
+        pv = (c_double * 6)(p[0].real, p[0].imag, p[1].real, p[1].imag, p[2].real, p[2].imag)
+        _check(load().vie_plane_wave(self.handle, float(k0), kh, pv, precision,
+                                     self._vec(out, precision, "out"), _stream()))
+        return out
+
+    def matvec(self, spec, x, y=None, precision=None):
+        precision = precision or (C128 if x.dtype == _dtype(C128) else C64)
+        y = self.empty(precision) if y is None else y
+        _check(load().vie_matvec(self.handle, spec.handle, precision, self._vec(x, precision, "x"),
+                                 self._vec(y, precision, "y"), _stream()))
+        return y
+
+    def precond(self, spec, b, y=None, inner_tol=1e-2, inner_maxit=100, precision=None):
+        precision = precision or (C128 if b.dtype == _dtype(C128) else C64)
+        y = self.empty(precision) if y is None else y
+        st = PrecondStats()
+        _check(load().vie_block_precond_apply(self.handle, spec.handle, precision, self._vec(b, precision, "b"),
+                                              self._vec(y, precision, "y"), float(inner_tol), int(inner_maxit),
+                                              _stream(), byref(st)))
+        return y, _struct_dict(st)
+
+    def solve(self, spec, einc, e=None, outer_tol=1e-6, inner_tol=1e-2, outer_maxit=1000, inner_maxit=100,
+              use_precond=True, mode=MODE_MIXED, max_refinements=0, wait_timeout_ms=0.0, check=True):
+        e = self.empty(C128) if e is None else e
+        o = SolveOpts(float(outer_tol), float(inner_tol), int(outer_maxit), int(inner_maxit), int(bool(use_precond)),
+                      int(mode), int(max_refinements), float(wait_timeout_ms))
+        st = SolveStats()
+        rc = load().vie_solve(self.handle, spec.handle, self._vec(einc, C128, "einc"), self._vec(e, C128, "e"),
+                              byref(o), _stream(), byref(st))
+        if check:
+            _check(rc, allow=(VIE_ENOTCONV,))
+        return e, _struct_dict(st)
+
+    def solve_host(self, spec, einc_host, out_host, **kw):
+        """End-to-end solve from pinned host memory: H2D copy, solve, D2H copy."""
+        import torch
+        dev = torch.empty((3,) + self.shape, dtype=torch.complex128, device="cuda")
+        dev.copy_(einc_host, non_blocking=True)
+        e, st = self.solve(spec, dev, **kw)
+        out_host.copy_(e, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return out_host, st

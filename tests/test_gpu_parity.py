@@ -1,0 +1,207 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against the CPU oracle.
+
+Tolerances (relative 2-norm over all entries):
+  * complex128 MVM: 1e-12 (FP64 FFTs; observed ~1e-15);
+  * complex64 MVM: 1e-5 (FP32 FFTs of length <= 512 per axis: a few units of
+    2^-24 per butterfly stage, ~20 stages in forward + inverse);
+  * preconditioner with tight inner tolerance (1e-12), complex128: 1e-9
+    (both sides approximate the exact block inverse);
+  * solves: relative field error vs the oracle solved to 1e-10.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mvm as omvm
+from oracle import precond as oprecond
+from oracle import solve as osolve
+from paper_2501_13512_gb300 import inputs, vie
+
+pytestmark = pytest.mark.gpu
+
+K0 = 2 * np.pi
+H = 0.05
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+SHAPES = [(16, 16, 16), (5, 7, 3), (12, 20, 9), (1, 1, 1), (33, 4, 2), (2, 1, 40), (64, 48, 8)]
+
+
+@pytest.mark.parametrize("n", SHAPES)
+def test_matvec_c128(n):
+    eps_r, _, x = inputs.random_case(n, seed=sum(n))
+    g = vie.Grid(eps_r, H)
+    sp = g.spectrum(K0)
+    y = g.matvec(sp, dev(x))
+    ref = omvm.FFTOperator(eps_r, H, K0)(x)
+    assert rel(host(y), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n", SHAPES)
+def test_matvec_c64(n):
+    eps_r, _, x = inputs.random_case(n, seed=sum(n) + 1)
+    g = vie.Grid(eps_r, H)
+    sp = g.spectrum(K0)
+    y = g.matvec(sp, dev(x, torch.complex64))
+    ref = omvm.FFTOperator(eps_r, H, K0)(x.astype(np.complex64).astype(np.complex128))
+    assert rel(host(y), ref) <= 1e-5
+
+
+def test_matvec_metasurface_full_size():
+    # the 256x256x16 metasurface grid (padded FFT 512x512x32), both precisions
+    w = inputs.metasurface()
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(3,) + w.eps_r.shape) + 1j * rng.normal(size=(3,) + w.eps_r.shape)
+    ref = omvm.FFTOperator(w.eps_r, w.h, w.k0)(x)
+    g = vie.Grid.from_workload(w)
+    sp = g.spectrum(w.k0)
+    assert rel(host(g.matvec(sp, dev(x))), ref) <= 1e-12
+    assert rel(host(g.matvec(sp, dev(x, torch.complex64))), ref) <= 1e-5
+
+
+def test_matvec_rejects_aliasing_and_bad_precision():
+    eps_r, _, x = inputs.random_case((4, 4, 4), seed=2)
+    g = vie.Grid(eps_r, H)
+    sp = g.spectrum(K0, vie.C128)
+    xd = dev(x)
+    lib = vie.load()
+    rc = lib.vie_matvec(g.handle, sp.handle, vie.C128, xd.data_ptr(), xd.data_ptr(), None)
+    assert rc == vie.VIE_EINVAL
+    rc = lib.vie_matvec(g.handle, sp.handle, vie.C64, xd.data_ptr(), g.empty(vie.C64).data_ptr(), None)
+    assert rc == vie.VIE_EINVAL
+
+
+def test_plane_wave():
+    n = (9, 6, 5)
+    g = vie.Grid(np.ones(n[::-1], complex), H)
+    khat = np.array([0.3, -0.5, 0.8])
+    khat /= np.linalg.norm(khat)
+    pol = np.array([1.0, 0.2j, -0.3 + 0.1j])
+    ref = osolve.plane_wave(n, H, K0, khat, pol)
+    assert rel(host(g.plane_wave(K0, khat, pol)), ref) <= 1e-13
+    assert rel(host(g.plane_wave(K0, khat, pol, precision=vie.C64)), ref) <= 1e-6
+
+
+def test_precond_tight_matches_oracle():
+    eps_r, bid, b = inputs.random_case((12, 10, 8), seed=31, block_grid=(4, 5, 4))
+    P = oprecond.BlockPreconditioner(eps_r, bid, H, K0, inner_tol=1e-12, inner_maxit=300)
+    ref = P(b)
+    g = vie.Grid(eps_r, H, bid)
+    sp = g.spectrum(K0)
+    y, st = g.precond(sp, dev(b), inner_tol=1e-12, inner_maxit=300)
+    assert st["nblocks"] == len(P.blocks)
+    assert st["not_converged"] == 0 and st["breakdowns"] == 0
+    assert rel(host(y), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", [vie.C128, vie.C64])
+def test_precond_loose_meets_inner_tolerance(precision):
+    # uneven blocks (ragged at the grid edge) solved to 1e-2: each block's own residual meets it
+    eps_r, bid, b = inputs.random_case((13, 11, 7), seed=17, block_grid=(5, 4, 7))
+    g = vie.Grid(eps_r, H, bid)
+    sp = g.spectrum(K0)
+    dt = torch.complex128 if precision == vie.C128 else torch.complex64
+    y, st = g.precond(sp, dev(b, dt), inner_tol=1e-2, inner_maxit=100)
+    y = host(y)
+    bb = b.astype(np.complex64).astype(np.complex128) if precision == vie.C64 else b
+    for blk in oprecond.find_blocks(bid):
+        sl = (slice(None),) + blk.slices
+        op = omvm.FFTOperator(eps_r[blk.slices], H, K0, mask=blk.mask)
+        bk = np.where(blk.mask[None], bb[sl], 0)
+        xk = np.where(blk.mask[None], y[sl], 0)
+        assert np.linalg.norm(bk - op(xk)) <= 1.01e-2 * np.linalg.norm(bk)
+    air = bid < 0
+    assert np.array_equal(y[:, air], bb[:, air])
+
+
+def test_precond_without_blocks_is_identity():
+    eps_r, _, b = inputs.random_case((6, 5, 4), seed=3)
+    g = vie.Grid(eps_r, H)
+    sp = g.spectrum(K0)
+    y, st = g.precond(sp, dev(b))
+    assert st["nblocks"] == 0
+    assert np.array_equal(host(y), b)
+
+
+def _sphere_case():
+    w = inputs.sphere()
+    ein = osolve.plane_wave(w.n, w.h, w.k0, w.khat, w.pol)
+    ref, _ = osolve.solve(w.eps_r, w.block_id, w.h, w.k0, ein, tol=1e-10, use_precond=False)
+    return w, ein, ref
+
+
+def test_solve_sphere_plain_c128():
+    w, ein, ref = _sphere_case()
+    _, info = osolve.solve(w.eps_r, w.block_id, w.h, w.k0, ein, tol=1e-6, use_precond=False)
+    g = vie.Grid.from_workload(w)
+    sp = g.spectrum(w.k0)
+    e, st = g.solve(sp, dev(ein), outer_tol=1e-6, use_precond=False, mode=vie.MODE_PLAIN_C128)
+    assert st["status"] == vie.VIE_OK
+    assert st["true_rel_res"] <= 1e-6
+    assert st["outer_iters"] == info["iters"]        # same recurrences in FP64
+    assert rel(host(e), ref) <= 1e-5
+
+
+def test_solve_sphere_mixed():
+    w, ein, ref = _sphere_case()
+    g = vie.Grid.from_workload(w)
+    sp = g.spectrum(w.k0)
+    e, st = g.solve(sp, dev(ein), outer_tol=1e-6, use_precond=False, mode=vie.MODE_MIXED)
+    assert st["status"] == vie.VIE_OK
+    assert st["true_rel_res"] <= 1e-6
+    assert rel(host(e), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", [vie.MODE_PLAIN_C128, vie.MODE_MIXED])
+def test_solve_metasurface_crop_preconditioned(mode):
+    w = inputs.metasurface(cells=3, seed=2)
+    ein = osolve.plane_wave(w.n, w.h, w.k0, w.khat, w.pol)
+    ref, _ = osolve.solve(w.eps_r, w.block_id, w.h, w.k0, ein, tol=1e-10, use_precond=True, inner_tol=1e-2)
+    g = vie.Grid.from_workload(w)
+    sp = g.spectrum(w.k0)
+    e, st = g.solve(sp, dev(ein), outer_tol=1e-6, inner_tol=1e-2, use_precond=True, mode=mode)
+    assert st["status"] == vie.VIE_OK
+    assert st["true_rel_res"] <= 1e-6
+    e = host(e)
+    A = omvm.FFTOperator(w.eps_r, w.h, w.k0)
+    assert np.linalg.norm(ein - A(e)) <= 1.05e-6 * np.linalg.norm(ein)
+    assert rel(e, ref) <= 1e-4
+    assert st["precond_applies"] > 0 and st["inner_iters"] > 0
+
+
+def test_solve_metasurface_full_size_mixed():
+    # the full 256x256x16 metasurface, the benchmark's workload: FP64 residual checked by the oracle
+    w = inputs.metasurface()
+    ein = osolve.plane_wave(w.n, w.h, w.k0, w.khat, w.pol)
+    g = vie.Grid.from_workload(w)
+    sp = g.spectrum(w.k0)
+    e, st = g.solve(sp, dev(ein), outer_tol=1e-6, inner_tol=1e-2, use_precond=True, mode=vie.MODE_MIXED)
+    assert st["status"] == vie.VIE_OK
+    e = host(e)
+    A = omvm.FFTOperator(w.eps_r, w.h, w.k0)
+    r = np.linalg.norm(ein - A(e)) / np.linalg.norm(ein)
+    assert r <= 1.05e-6
+    assert abs(r - st["true_rel_res"]) <= 1e-3 * r
+
+
+def test_solve_zero_rhs():
+    eps_r, bid, _ = inputs.random_case((6, 5, 4), seed=3, block_grid=(3, 3, 2))
+    g = vie.Grid(eps_r, H, bid)
+    sp = g.spectrum(K0)
+    z = torch.zeros((3, 4, 5, 6), dtype=torch.complex128, device="cuda")
+    for mode in (vie.MODE_PLAIN_C128, vie.MODE_MIXED):
+        e, st = g.solve(sp, z, mode=mode)
+        assert st["status"] == vie.VIE_OK
+        assert not np.any(host(e))
