@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the block-preconditioned VIE-FFT solver on one GB300 (or N replicas).
+
+A step is one complete solve of the 256x256x16 focusing-metasurface workload
+(16 x 16 dielectric pillars, eps_r 6.25, h = lambda0/20, one block per pillar:
+256 uneven blocks; inner BiCGSTAB tolerance 1e-2, outer FP64 residual 1e-6),
+in mixed precision: FP64 residuals and scalars, complex64 FFT-MVMs and block
+solves. `value` is solves/s with inputs resident in HBM; the same line reports
+the plain FP64 (complex128) solve, full-grid MVMs/s in both precisions, p50/p99
+step latency, an end-to-end figure through the host-buffer API, the roofline of
+the dominant kernel (CUDA-event durations from the library's launch profile),
+the GPU clocks sampled during the timed region, and the CPU oracle timed on a
+bounded sample as a baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own replica: the solves are
+independent, there is no data exchange (weak scaling).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VIE-FFT MVMs/s & solves/s at rel-res 1e-6, mixed vs FP64 plain; p50/p99 latency"
+WORKLOAD = "metasurface-256x256x16"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "metasurface_reference.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    return ap.parse_args()
+
+
+def config(extra=None):
+    c = {"workload": WORKLOAD, "grid": [256, 256, 16], "padded_fft": [512, 512, 32], "unknowns": 3 * 256 * 256 * 16,
+         "blocks": 256, "block_fft": [32, 32, 32], "inner_tol": 1e-2, "outer_tol": 1e-6,
+         "mode": "mixed: FP64 residual/scalars, complex64 FFT-MVM and block solves",
+         "l2": "working set > L2 (about 1.5 GB touched per solve); no flush",
+         "spectrum": "Green spectra cached per (grid, wavelength), built before the timed region"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------- CPU oracle sample (baseline only)
+class OracleSample:
+    """The oracle's constituents of one outer iteration, timed on a bounded sample.
+
+    One full-grid FFT-MVM, and the inner block solves (Eq. 10) of every
+    block_stride-th block, timed separately; per-iteration cost = 2 MVMs + 2
+    full block-preconditioner applies (the sampled blocks scaled to all
+    blocks). Operator set-up (spectra) happens once, outside the timing, as the
+    GPU path caches its spectra too."""
+
+    def __init__(self, w, block_stride=4):
+        from oracle import mvm as omvm
+        from oracle import precond as oprecond
+        from oracle import solve as osolve
+        self.w = w
+        self.ein = osolve.plane_wave(w.n, w.h, w.k0, w.khat, w.pol)
+        self.A = omvm.FFTOperator(w.eps_r, w.h, w.k0)
+        self.blocks = oprecond.find_blocks(w.block_id)
+        self.sub = self.blocks[::block_stride]
+        self.ops = [omvm.FFTOperator(w.eps_r[b.slices], w.h, w.k0, mask=b.mask) for b in self.sub]
+
+    def run(self):
+        from oracle import krylov as okrylov
+        t0 = time.perf_counter()
+        self.A(self.ein)
+        t_mvm = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for b, op in zip(self.sub, self.ops):
+            sl = (slice(None),) + b.slices
+            bk = np.where(b.mask[None], self.ein[sl], 0.0)
+            okrylov.bicgstab(op.apply, bk, self.w.inner_tol, 100)
+        t_blocks = time.perf_counter() - t0
+        t_pre = t_blocks * len(self.blocks) / len(self.sub)
+        return {"t_mvm": t_mvm, "t_precond": t_pre, "t_iter": 2 * t_mvm + 2 * t_pre,
+                "sample": f"1 full-grid oracle FFT-MVM + inner block solves of {len(self.sub)} of "
+                          f"{len(self.blocks)} blocks ({t_mvm + t_blocks:.1f} s of CPU), scaled to one outer "
+                          f"iteration (2 MVMs + 2 preconditioner applies)"}
+
+
+def outer_iters_reference(default):
+    if os.path.exists(GOLDEN):
+        with open(GOLDEN) as f:
+            return float(json.load(f)["outer_iters"]), "oracle full solve (tests/golden/metasurface_reference.json)"
+    return float(default), "plain FP64 GPU solve (same recurrences as the oracle)"
+
+
+def run_reference(args, rank):
+    """--impl reference: the CPU oracle, as it stands, timed on this host's cores."""
+    if rank != 0:
+        return
+    from paper_2501_13512_gb300 import inputs
+    w = inputs.metasurface()
+    iters, src = outer_iters_reference(20.0)
+    times = []
+    sample = ""
+    smp = OracleSample(w, block_stride=16)
+    for i in range(args.warmup + args.steps):
+        s = smp.run()
+        sample = s["sample"]
+        if i >= args.warmup:
+            times.append(s["t_iter"] * iters)
+    t = float(np.mean(times))
+    v = 1.0 / t
+    line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
+            "config": config({"mode": "oracle: numpy complex128, block-preconditioned BiCGSTAB"}),
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample + f"; x {iters:g} outer iterations from the {src}"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2501_13512_gb300 import build, inputs, vie
+    if not os.path.exists(vie.LIB_PATH):
+        build.build()
+    w = inputs.metasurface()
+    g = vie.Grid.from_workload(w)
+    sp = g.spectrum(w.k0)
+    einc = g.plane_wave(w.k0, w.khat, w.pol)
+    e = g.empty()
+    stream = torch.cuda.current_stream()
+    opts = dict(outer_tol=w.outer_tol, inner_tol=w.inner_tol, use_precond=True, mode=vie.MODE_MIXED)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        _, st = g.solve(sp, einc, e, **opts)
+    sampler = ClockSampler(local)
+    if not args.no_profile:
+        vie.profile_enable(True)
+    launches0 = vie.launch_count()
+    sampler.start()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    stats = []
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        _, st = g.solve(sp, einc, e, **opts)
+        ev[i][1].record(stream)
+        stats.append(st)
+    t_all1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = vie.launch_count() - launches0
+    kstats = []
+    if not args.no_profile:
+        kstats, _ = vie.profile_read()
+        vie.profile_enable(False)
+    elapsed = t_all0.elapsed_time(t_all1) / 1e3
+    lat = np.array([a.elapsed_time(b) for a, b in ev])
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = args.steps * world / elapsed
+    e_mixed = e.clone()
+
+    # full-grid MVM throughput in both precisions
+    def time_mvm(prec, reps):
+        x = einc if prec == vie.C128 else einc.to(torch.complex64)
+        y = g.empty(prec)
+        g.matvec(sp, x, y)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            g.matvec(sp, x, y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return reps / (a.elapsed_time(b) / 1e3)
+    mvm64 = time_mvm(vie.C64, 20)
+    mvm128 = time_mvm(vie.C128, 5)
+
+    # plain FP64 solve of the same problem
+    plain = None
+    if args.plain_steps > 0:
+        pl = []
+        e_plain = g.empty()
+        for _ in range(args.plain_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, pst = g.solve(sp, einc, e_plain, outer_tol=w.outer_tol, inner_tol=w.inner_tol, use_precond=True,
+                             mode=vie.MODE_PLAIN_C128)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pl.append(a.elapsed_time(b))
+        diff = float(torch.linalg.vector_norm(e_mixed - e_plain) / torch.linalg.vector_norm(e_plain))
+        plain = {"solves_per_s": 1e3 / float(np.mean(pl)), "ms": float(np.mean(pl)),
+                 "outer_iters": pst["outer_iters"], "true_rel_res": pst["true_rel_res"],
+                 "matvecs_c128": pst["matvecs_c128"], "inner_iters": pst["inner_iters"],
+                 "mixed_vs_plain_rel_field_diff": diff}
+
+    # field error against the oracle's full solve at seeded sample voxels
+    accuracy = None
+    if os.path.exists(GOLDEN):
+        gd = json.load(open(GOLDEN))
+        idx = torch.tensor(gd["sample_index"], device="cuda")
+        ref = np.array(gd["sample_re"]) + 1j * np.array(gd["sample_im"])
+        got = e_mixed.reshape(-1)[idx].cpu().numpy()
+        accuracy = {"sampled_rel_field_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                    "oracle_outer_iters": gd["outer_iters"], "samples": len(ref)}
+
+    # end to end through the host-buffer API: pinned E_inc in, E out, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        h_in = einc.cpu().pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g.solve_host(sp, h_in, h_out, **opts)
+        t1 = time.perf_counter()
+        nbytes = h_in.numel() * h_in.element_size()
+        e2e = {"value": args.e2e_steps / (t1 - t0), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+
+    # roofline of the dominant kernel kind over the timed region
+    peak, peak_src = peaks()
+    roof = None
+    if kstats:
+        dom = max(kstats, key=lambda k: k["total_ms"])
+        tot = sum(k["total_ms"] for k in kstats)
+        per_launch_ms = dom["total_ms"] / dom["launches"]
+        bytes_per_launch = dom["bytes"] / dom["launches"]
+        ach = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": f"{dom['name']}_{dom['precision']}",
+                "launches": dom["launches"], "ms_per_launch": per_launch_ms,
+                "algorithmic_bytes_per_launch": bytes_per_launch, "share_of_kernel_time": dom["total_ms"] / tot,
+                "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        kernels = {f"{k['name']}_{k['precision']}": {"launches": k["launches"], "ms": round(k["total_ms"], 3),
+                                                     "GBps": round(k["bytes"] / (k["total_ms"] * 1e-3) / 1e9, 1)}
+                   for k in sorted(kstats, key=lambda k: -k["total_ms"])}
+    else:
+        kernels = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters, src = outer_iters_reference(plain["outer_iters"] if plain else 20)
+        s = OracleSample(w, block_stride=4).run()
+        v = 1.0 / (s["t_iter"] * iters)
+        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": s["sample"] + f"; x {iters:g} outer iterations from the {src}",
+               "oracle_mvm_s": s["t_mvm"], "host_cores": os.cpu_count()}
+
+    last = stats[-1]
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+            "config": config({"parallelism": "replicas" if world > 1 else "single GPU"}),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "mvm_per_s": {"c64": mvm64 * world, "c128": mvm128 * world},
+            "solve": {"outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
+                      "precond_applies": last["precond_applies"], "matvecs_c128": last["matvecs_c128"],
+                      "matvecs_c64": last["matvecs_c64"], "refinements": last["refinements"],
+                      "true_rel_res": last["true_rel_res"]},
+            "plain_c128": plain, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "kernels": kernels, "clocks": clocks, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

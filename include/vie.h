@@ -182,6 +182,31 @@ int vie_solve(vie_grid* grid, const vie_spectrum* spectrum, const void* einc_dev
               void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
               vie_solve_stats* stats);
 
+/* Kernel-level profile, aggregated per kernel kind and precision. */
+typedef struct {
+    char name[32];           /* x_fwd, y_fwd, z_green, y_inv, x_inv, bicg_update,
+                                bicg_dot, spectrum, field                          */
+    int32_t precision;       /* VIE_C128 or VIE_C64                                 */
+    int64_t launches;        /* launches recorded                                   */
+    double total_ms;         /* sum of CUDA-event durations, each measured on the
+                                launching stream                                    */
+    double bytes;            /* algorithmic bytes: inputs read + outputs written by
+                                the work units (boxes, segments) each launch
+                                actually processed                                  */
+} vie_kernel_stat;
+
+/* enable = 1 clears the profile and starts recording every launch of this
+ * library in this process (CUDA events around each launch); 0 stops. The
+ * recording itself adds two event records per launch. Errors: VIE_ECUDA. */
+int vie_profile_enable(int enable);
+
+/* Waits for the recorded work, then writes up to cap aggregated entries to
+ * out (n_out receives the count) and the number of kernel launches the
+ * library made since the process started to total_launches (counted whether
+ * or not profiling is enabled). Any pointer may be NULL. Errors: VIE_ECUDA,
+ * VIE_ENOMEM (more launches than the profile holds: 1,048,576). */
+int vie_profile_read(vie_kernel_stat* out, int cap, int* n_out, int64_t* total_launches);
+
 /* Copies the text of the last error on this thread into buf (NUL-terminated,
  * truncated to len). Returns the length of the full message. */
 int vie_last_error(char* buf, size_t len);

@@ -115,6 +115,7 @@ template <class C> struct RowArgs {
     int rows_per_box;    // 3 * bz * by
     int plane;           // bz * by
     int bx;
+    int* units;          // profiling: boxes processed (null when off)
 };
 
 template <class C, int MODE>
@@ -125,6 +126,11 @@ __global__ void __launch_bounds__(kThreads) k_rows(RowArgs<C> a) {
     const int pitch = TR + 1;          // odd pitch: conflict-free transposed staging
     const int L = 1 << a.lL;
     const int64_t row0 = (int64_t)blockIdx.x * TR;
+    if (a.units != nullptr && threadIdx.x == 0) {
+        const int64_t rpb = a.rows_per_box;
+        for (int64_t b = (row0 + rpb - 1) / rpb; b * rpb < row0 + TR && b * rpb < a.nrows; ++b)
+            if (box_active(a.st, (int)b)) atomicAdd(a.units, 1);
+    }
 
     for (int idx = threadIdx.x; idx < TR * a.n_in; idx += blockDim.x) {
         int r = idx / a.n_in, i = idx - r * a.n_in;
@@ -178,6 +184,7 @@ template <class C> struct ColArgs {
     int ncols, n_in, n_out, lL, ltc, twshift;
     int64_t in_axis, out_axis, in_s1, out_s1, in_s2, out_s2;
     int b2_per_box;      // blockIdx.z / b2_per_box = box index
+    int* units;
 };
 
 template <class C, bool FWD>
@@ -188,6 +195,9 @@ __global__ void __launch_bounds__(kThreads) k_cols(ColArgs<C> a) {
     const int L = 1 << a.lL;
     const int col0 = blockIdx.x * TC;
     if (!box_active(a.st, blockIdx.z / a.b2_per_box)) return;   // uniform per CTA
+    if (a.units != nullptr && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 &&
+        blockIdx.z % a.b2_per_box == 0)
+        atomicAdd(a.units, 1);
     const C* in = a.in + blockIdx.z * a.in_s2 + blockIdx.y * a.in_s1 + col0;
     C* out = a.out + blockIdx.z * a.out_s2 + blockIdx.y * a.out_s1 + col0;
     const int ncol = min(TC, a.ncols - col0);
@@ -214,6 +224,7 @@ template <class C> struct ZArgs {
     const C* tw;
     int ncols, nzb, lL, ltc, twshift;
     int64_t axis, comp_stride, box_stride, gcomp;
+    int* units;
 };
 
 template <class C>
@@ -226,6 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_zgreen(ZArgs<C> a) {
     const int col0 = blockIdx.x * TC;
     const int b = blockIdx.y;
     if (!box_active(a.st, b)) return;
+    if (a.units != nullptr && threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(a.units, 1);
     C* w = a.w + b * a.box_stride + col0;
     const int ncol = min(TC, a.ncols - col0);
 
@@ -286,21 +298,29 @@ static int prep_smem(K kernel, size_t bytes) {
     return VIE_OK;
 }
 
+struct Prof {
+    int kind;
+    int64_t bpu, fixed;
+};
+template <class C> static int prec_code() { return sizeof(C) == 16 ? VIE_C128 : VIE_C64; }
+
 template <class C, int MODE>
-static int launch_rows(RowArgs<C> a, cudaStream_t s) {
+static int launch_rows(RowArgs<C> a, Prof pf, cudaStream_t s) {
     a.ltr = pick_ltile(a.lL, sizeof(C), 1, 1);
     const int TR = 1 << a.ltr;
     size_t smem = (size_t)(1 << a.lL) * (TR + 1) * sizeof(C);
     VIE_TRY(prep_smem(k_rows<C, MODE>, smem));
     int64_t grid = (a.nrows + TR - 1) / TR;
     if (grid <= 0) return VIE_OK;
+    a.units = prof_begin(s, pf.kind, prec_code<C>(), pf.bpu, pf.fixed, true);
     k_rows<C, MODE><<<(unsigned)grid, kThreads, smem, s>>>(a);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
 
 template <class C, bool FWD>
-static int launch_cols(ColArgs<C> a, int nb1, int nb2, cudaStream_t s) {
+static int launch_cols(ColArgs<C> a, int nb1, int nb2, Prof pf, cudaStream_t s) {
     a.ltc = pick_ltile(a.lL, sizeof(C), 1, 0);
     if ((1 << a.ltc) > a.ncols) a.ltc = ilog2(a.ncols) - ((1 << ilog2(a.ncols)) > a.ncols ? 1 : 0);
     if (a.ltc < 0) a.ltc = 0;
@@ -308,13 +328,15 @@ static int launch_cols(ColArgs<C> a, int nb1, int nb2, cudaStream_t s) {
     size_t smem = (size_t)(1 << a.lL) * TC * sizeof(C);
     VIE_TRY(prep_smem(k_cols<C, FWD>, smem));
     dim3 grid((a.ncols + TC - 1) / TC, nb1, nb2);
+    a.units = prof_begin(s, pf.kind, prec_code<C>(), pf.bpu, pf.fixed, true);
     k_cols<C, FWD><<<grid, kThreads, smem, s>>>(a);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
 
 template <class C>
-static int launch_zgreen(ZArgs<C> a, int nb, cudaStream_t s) {
+static int launch_zgreen(ZArgs<C> a, int nb, Prof pf, cudaStream_t s) {
     a.ltc = pick_ltile(a.lL, sizeof(C), 3, 0);
     if ((1 << a.ltc) > a.ncols) a.ltc = ilog2(a.ncols) - ((1 << ilog2(a.ncols)) > a.ncols ? 1 : 0);
     if (a.ltc < 0) a.ltc = 0;
@@ -322,7 +344,9 @@ static int launch_zgreen(ZArgs<C> a, int nb, cudaStream_t s) {
     size_t smem = (size_t)(1 << a.lL) * 3 * TC * sizeof(C);
     VIE_TRY(prep_smem(k_zgreen<C>, smem));
     dim3 grid((a.ncols + TC - 1) / TC, nb);
+    a.units = prof_begin(s, pf.kind, prec_code<C>(), pf.bpu, pf.fixed, true);
     k_zgreen<C><<<grid, kThreads, smem, s>>>(a);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -339,6 +363,17 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     C* w1 = reinterpret_cast<C*>(bs.w1);
     C* w2 = reinterpret_cast<C*>(bs.w2);
     const int64_t planeXY = (int64_t)bs.Mx * bs.My;
+    // algorithmic bytes per box of each pass (inputs read + outputs written)
+    const int64_t es = sizeof(C);
+    const int64_t box = bs.box_elems();
+    const int64_t b1 = 3LL * bs.bz * bs.by * bs.Mx * es;          // w1 per box
+    const int64_t b2 = 3LL * bs.bz * planeXY * es;                // w2 per box
+    const int64_t bv = 3LL * box * es;                            // x or y per box
+    const Prof px{PK_X_FWD, bv + box * es + b1, 0};
+    const Prof py{PK_Y_FWD, b1 + b2, 0};
+    const Prof pz{PK_Z_GREEN, 2 * b2, 6LL * bs.Mz * planeXY * es};
+    const Prof piy{PK_Y_INV, b2 + b1, 0};
+    const Prof pix{PK_X_INV, b1 + 2 * bv + (bs.mask ? box : 0), 0};
 
     // pass X: chi * x, zero-padded forward FFT of every row
     RowArgs<C> rx{};
@@ -347,7 +382,7 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     rx.in_stride = bs.bx; rx.out_stride = bs.Mx; rx.n_in = bs.bx; rx.n_out = bs.Mx;
     rx.lL = bs.lx; rx.twshift = kLogLmax - bs.lx;
     rx.rows_per_box = 3 * bs.bz * bs.by; rx.plane = bs.bz * bs.by; rx.bx = bs.bx;
-    VIE_TRY((launch_rows<C, ROW_FWD_CHI>(rx, s)));
+    VIE_TRY((launch_rows<C, ROW_FWD_CHI>(rx, px, s)));
 
     // pass Y forward
     ColArgs<C> cy{};
@@ -357,7 +392,7 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     cy.in_s1 = (int64_t)bs.by * bs.Mx; cy.out_s1 = planeXY;
     cy.in_s2 = (int64_t)bs.bz * bs.by * bs.Mx; cy.out_s2 = (int64_t)bs.bz * planeXY;
     cy.b2_per_box = 3;
-    VIE_TRY((launch_cols<C, true>(cy, bs.bz, bs.nb * 3, s)));
+    VIE_TRY((launch_cols<C, true>(cy, bs.bz, bs.nb * 3, py, s)));
 
     // pass Z: forward, Green multiply, inverse
     ZArgs<C> z{};
@@ -365,20 +400,20 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     z.ncols = (int)planeXY; z.nzb = bs.bz; z.lL = bs.lz; z.twshift = kLogLmax - bs.lz;
     z.axis = planeXY; z.comp_stride = (int64_t)bs.bz * planeXY; z.box_stride = 3 * z.comp_stride;
     z.gcomp = (int64_t)bs.Mz * planeXY;
-    VIE_TRY(launch_zgreen<C>(z, bs.nb, s));
+    VIE_TRY(launch_zgreen<C>(z, bs.nb, pz, s));
 
     // pass Y inverse: keep y < by
     ColArgs<C> iy = cy;
     iy.in = w2; iy.out = w1; iy.n_in = bs.My; iy.n_out = bs.by;
     iy.in_s1 = planeXY; iy.out_s1 = (int64_t)bs.by * bs.Mx;
     iy.in_s2 = (int64_t)bs.bz * planeXY; iy.out_s2 = (int64_t)bs.bz * bs.by * bs.Mx;
-    VIE_TRY((launch_cols<C, false>(iy, bs.bz, bs.nb * 3, s)));
+    VIE_TRY((launch_cols<C, false>(iy, bs.bz, bs.nb * 3, piy, s)));
 
     // pass X inverse: keep x < bx, y = x - u
     RowArgs<C> ix = rx;
     ix.in = w1; ix.out = y; ix.xin = x; ix.mask = bs.mask; ix.chi = nullptr;
     ix.in_stride = bs.Mx; ix.out_stride = bs.bx; ix.n_in = bs.Mx; ix.n_out = bs.bx;
-    VIE_TRY((launch_rows<C, ROW_INV_UPDATE>(ix, s)));
+    VIE_TRY((launch_rows<C, ROW_INV_UPDATE>(ix, pix, s)));
     return VIE_OK;
 }
 
@@ -389,6 +424,7 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s) {
     const C* T = tw_ptr<C>(tw);
     const int64_t planeXY = (int64_t)bs.Mx * bs.My;
     const int64_t vol = planeXY * bs.Mz;
+    const int64_t es = sizeof(C);
 
     RowArgs<C> rx{};
     rx.in = G; rx.out = G; rx.tw = T;
@@ -396,7 +432,7 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s) {
     rx.in_stride = bs.Mx; rx.out_stride = bs.Mx; rx.n_in = bs.Mx; rx.n_out = bs.Mx;
     rx.lL = bs.lx; rx.twshift = kLogLmax - bs.lx;
     rx.rows_per_box = (int)std::min<int64_t>(rx.nrows, 1 << 30); rx.plane = 1; rx.bx = bs.Mx;
-    VIE_TRY((launch_rows<C, ROW_FWD_PLAIN>(rx, s)));
+    VIE_TRY((launch_rows<C, ROW_FWD_PLAIN>(rx, Prof{PK_SPECTRUM, 12 * vol * es, 0}, s)));
 
     ColArgs<C> cy{};
     cy.in = G; cy.out = G; cy.tw = T; cy.b2_per_box = 1;
@@ -404,7 +440,7 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s) {
     cy.in_axis = cy.out_axis = bs.Mx;
     cy.in_s1 = cy.out_s1 = planeXY;
     cy.in_s2 = cy.out_s2 = vol;
-    VIE_TRY((launch_cols<C, true>(cy, bs.Mz, 6, s)));
+    VIE_TRY((launch_cols<C, true>(cy, bs.Mz, 6, Prof{PK_SPECTRUM, 2 * vol * es, 0}, s)));
 
     ColArgs<C> cz{};
     cz.in = G; cz.out = G; cz.tw = T; cz.b2_per_box = 1;
@@ -412,7 +448,7 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s) {
     cz.in_axis = cz.out_axis = planeXY;
     cz.in_s1 = cz.out_s1 = 0;
     cz.in_s2 = cz.out_s2 = vol;
-    VIE_TRY((launch_cols<C, true>(cz, 1, 6, s)));
+    VIE_TRY((launch_cols<C, true>(cz, 1, 6, Prof{PK_SPECTRUM, 2 * vol * es, 0}, s)));
     return VIE_OK;
 }
 

@@ -77,8 +77,10 @@ int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t
     // (1 + j ka)(c - j sn) = c + ka sn + j (ka c - sn)
     double2 self = make_double2((2.0 / 3.0) * (c + ka * sn - 1.0) - 1.0 / 3.0, (2.0 / 3.0) * (ka * c - sn));
     const double scale = 1.0 / ((double)bs.Mx * bs.My * bs.Mz);
+    prof_begin(s, PK_SPECTRUM, VIE_C128, 0, 6 * bs.spec_elems() * 16, false);
     k_green_sample<<<grid_1d(bs.spec_elems()), 256, 0, s>>>(G, bs.Mx, bs.My, bs.Mz, bs.bx, bs.by, bs.bz,
                                                             k0, h, scale, self);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -88,7 +90,9 @@ __global__ void k_c128_to_c64(const double2* a, float2* b, int64_t n) {
         b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 int convert_c128_to_c64(const double2* a, float2* b, int64_t n, cudaStream_t s) {
+    prof_begin(s, PK_SPECTRUM, VIE_C64, 0, n * 24, false);
     k_c128_to_c64<<<grid_1d(n), 256, 0, s>>>(a, b, n);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -117,10 +121,12 @@ int plane_wave_launch(const vie_grid* g, double k0, const double* khat, const do
                       int precision, void* out, cudaStream_t s) {
     double3 kh = make_double3(khat[0], khat[1], khat[2]);
     double2 p0 = make_double2(pol[0], pol[1]), p1 = make_double2(pol[2], pol[3]), p2 = make_double2(pol[4], pol[5]);
+    prof_begin(s, PK_FIELD, precision, 0, 3 * g->N * (precision == VIE_C128 ? 16 : 8), false);
     if (precision == VIE_C128)
         k_plane_wave<double2><<<grid_1d(g->N), 256, 0, s>>>((double2*)out, g->nx, g->ny, g->nz, g->h, k0, kh, p0, p1, p2);
     else
         k_plane_wave<float2><<<grid_1d(g->N), 256, 0, s>>>((float2*)out, g->nx, g->ny, g->nz, g->h, k0, kh, p0, p1, p2);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -184,8 +190,10 @@ __global__ void k_copy_unblocked(const C* b, C* y, const int32_t* block_id, int6
 template <class C>
 int precond_gather(const vie_grid* g, const Group& gr, const C* b, C* out, cudaStream_t s) {
     const BoxSet& bs = gr.bs;
+    prof_begin(s, PK_FIELD, sizeof(C) == 16 ? VIE_C128 : VIE_C64, 0, 2 * bs.nb * bs.vec_elems() * (int64_t)sizeof(C), false);
     k_gather<C><<<grid_1d(bs.nb * bs.vec_elems()), 256, 0, s>>>(b, out, bs.mask, bs.origin, bs.nb, bs.bx, bs.by,
                                                                 bs.bz, g->nx, g->ny, g->nz);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -193,15 +201,19 @@ int precond_gather(const vie_grid* g, const Group& gr, const C* b, C* out, cudaS
 template <class C>
 int precond_scatter_group(const vie_grid* g, const Group& gr, const C* xk, C* y, cudaStream_t s) {
     const BoxSet& bs = gr.bs;
+    prof_begin(s, PK_FIELD, sizeof(C) == 16 ? VIE_C128 : VIE_C64, 0, 2 * bs.nb * bs.vec_elems() * (int64_t)sizeof(C), false);
     k_scatter<C><<<grid_1d(bs.nb * bs.vec_elems()), 256, 0, s>>>(xk, y, bs.mask, bs.origin, bs.nb, bs.bx, bs.by,
                                                                  bs.bz, g->nx, g->ny, g->nz);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
 
 template <class C>
 int precond_copy_unblocked(const vie_grid* g, const C* b, C* y, cudaStream_t s) {
+    prof_begin(s, PK_FIELD, sizeof(C) == 16 ? VIE_C128 : VIE_C64, 0, g->N * 4 + 6 * g->N * (int64_t)sizeof(C), false);
     k_copy_unblocked<C><<<grid_1d(g->N), 256, 0, s>>>(b, y, g->block_id, g->N);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }

@@ -31,6 +31,7 @@ template <class C> struct VecArgs {
     int maxcta;
     double tol;
     int maxit;
+    int* units;         // profiling: active segments processed
 };
 
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg(VecArgs<C> a) {
         const int need = (OP == OP_XHALF) ? SEG_HALF_PENDING : SEG_ACTIVE;
         if (S.status != need) return;       // same value for every CTA of the segment
     }
+    if (a.units != nullptr && threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(a.units, 1);
     const int64_t off = (int64_t)seg * a.seglen;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     C acc1 = czero<C>(), acc2 = czero<C>();
@@ -228,6 +230,11 @@ static int launch_bicg(Bicg<C>& k, int op, double tol, int maxit, cudaStream_t s
     int64_t want = (k.seglen + (int64_t)kRedThreads * 8 - 1) / ((int64_t)kRedThreads * 8);
     int nct = (int)std::max<int64_t>(1, std::min<int64_t>(want, kMaxCtaPerSeg));
     dim3 grid(nct, k.nseg);
+    // vectors touched per segment by each op (reads + writes)
+    static const int nvec[] = {6, 4, 3, 3, 7, 2, 2, 2};
+    const bool dot = op == OP_RHO || op == OP_SIGMA || op == OP_OMEGA;
+    a.units = prof_begin(s, dot ? PK_BICG_DOT : PK_BICG_UPDATE, sizeof(C) == 16 ? VIE_C128 : VIE_C64,
+                         (int64_t)nvec[op] * k.seglen * (int64_t)sizeof(C), 0, true);
     switch (op) {
         case OP_INIT: k_bicg<C, OP_INIT><<<grid, kRedThreads, 0, s>>>(a); break;
         case OP_P: k_bicg<C, OP_P><<<grid, kRedThreads, 0, s>>>(a); break;
@@ -237,8 +244,9 @@ static int launch_bicg(Bicg<C>& k, int op, double tol, int maxit, cudaStream_t s
         case OP_RHO: k_bicg<C, OP_RHO><<<grid, kRedThreads, 0, s>>>(a); break;
         case OP_SIGMA: k_bicg<C, OP_SIGMA><<<grid, kRedThreads, 0, s>>>(a); break;
         case OP_OMEGA: k_bicg<C, OP_OMEGA><<<grid, kRedThreads, 0, s>>>(a); break;
-        default: return fail(VIE_EINVAL, "bad BiCGSTAB op");
+        default: prof_end(s); return fail(VIE_EINVAL, "bad BiCGSTAB op");
     }
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -281,7 +289,9 @@ static unsigned grid_for(int64_t n) {
 }
 
 template <class C> int vec_copy(const C* a, C* b, int64_t n, cudaStream_t s) {
+    prof_begin(s, PK_FIELD, sizeof(C) == 16 ? VIE_C128 : VIE_C64, 0, 2 * n * (int64_t)sizeof(C), false);
     k_copy<C><<<grid_for(n), 256, 0, s>>>(a, b, n);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -293,7 +303,9 @@ __global__ void k_residual128(const double2* b, const double2* ax, double2* r, i
         r[i] = b[i] - ax[i];
 }
 int vec_residual128(const double2* b, const double2* ax, double2* r, int64_t n, cudaStream_t s) {
+    prof_begin(s, PK_FIELD, VIE_C128, 0, 3 * n * 16, false);
     k_residual128<<<grid_for(n), 256, 0, s>>>(b, ax, r, n);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -327,7 +339,9 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const double2* a, int64_t
 int vec_norm2_128(const double2* a, int64_t n, ReduceScratch* red, double* d_out, cudaStream_t s) {
     int64_t want = (n + (int64_t)kRedThreads * 8 - 1) / ((int64_t)kRedThreads * 8);
     int nct = (int)std::max<int64_t>(1, std::min<int64_t>(want, kMaxCtaPerSeg));
+    prof_begin(s, PK_FIELD, VIE_C128, 0, n * 16, false);
     k_norm2<<<nct, kRedThreads, 0, s>>>(a, n, red->part, red->count, d_out);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -341,7 +355,9 @@ __global__ void k_scale_to_c64(const double2* a, const double* norm2, float2* b,
     }
 }
 int vec_scale_to_c64(const double2* a, const double* d_norm2, float2* b, int64_t n, cudaStream_t s) {
+    prof_begin(s, PK_FIELD, VIE_C128, 0, n * 24, false);
     k_scale_to_c64<<<grid_for(n), 256, 0, s>>>(a, d_norm2, b, n);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
@@ -356,7 +372,9 @@ __global__ void k_add_scaled_c64(double2* x, const float2* d, const double* norm
     }
 }
 int vec_add_scaled_c64(double2* x, const float2* d, const double* d_norm2, int64_t n, cudaStream_t s) {
+    prof_begin(s, PK_FIELD, VIE_C128, 0, n * 40, false);
     k_add_scaled_c64<<<grid_for(n), 256, 0, s>>>(x, d, d_norm2, n);
+    prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }

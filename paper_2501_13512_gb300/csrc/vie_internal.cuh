@@ -169,6 +169,21 @@ struct vie_grid {
 
 namespace vie {
 
+// ---------------------------------------------------------------- launch profiling (profile.cu)
+// Every kernel launch of the library goes through prof_begin / prof_end. When
+// profiling is off only a launch counter is incremented. When on, CUDA events
+// bracket the launch on its stream, and the kernel receives a device counter
+// to which it adds the number of work units (boxes or segments) it actually
+// processed, so the algorithmic bytes of launches that skip converged blocks
+// are counted exactly: bytes = units * bytes_per_unit + (units ? fixed : 0).
+enum ProfKind {
+    PK_X_FWD = 0, PK_Y_FWD, PK_Z_GREEN, PK_Y_INV, PK_X_INV,
+    PK_BICG_UPDATE, PK_BICG_DOT, PK_SPECTRUM, PK_FIELD, PK_COUNT
+};
+int* prof_begin(cudaStream_t s, int kind, int precision, int64_t bytes_per_unit, int64_t bytes_fixed,
+                bool device_units);
+void prof_end(cudaStream_t s);
+
 // ---------------------------------------------------------------- launchers (fft.cu)
 template <class C>
 int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st,

@@ -58,6 +58,11 @@ class SolveStats(ctypes.Structure):
                 ("true_rel_res", c_double), ("status", c_int32)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("precision", c_int32), ("launches", c_int64),
+                ("total_ms", c_double), ("bytes", c_double)]
+
+
 def _struct_dict(s):
     return {name: getattr(s, name) for name, _ in s._fields_}
 
@@ -92,6 +97,8 @@ def load(path=LIB_PATH):
         "vie_matvec": ([P, P, c_int, P, P, P], c_int),
         "vie_block_precond_apply": ([P, P, c_int, P, P, c_double, c_int, P, POINTER(PrecondStats)], c_int),
         "vie_solve": ([P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
+        "vie_profile_enable": ([c_int], c_int),
+        "vie_profile_read": ([POINTER(KernelStat), c_int, POINTER(c_int), POINTER(c_int64)], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -112,6 +119,33 @@ def _check(rc, allow=()):
     if rc != VIE_OK and rc not in allow:
         raise VieError(rc, last_error())
     return rc
+
+
+def profile_enable(on=True):
+    """Start (clearing) or stop CUDA-event recording of every library launch."""
+    _check(load().vie_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """(per-kernel stats list, total launches since process start)."""
+    cap = 64
+    arr = (KernelStat * cap)()
+    n = c_int()
+    tot = c_int64()
+    _check(load().vie_profile_read(arr, cap, byref(n), byref(tot)))
+    out = []
+    for i in range(n.value):
+        d = _struct_dict(arr[i])
+        d["name"] = arr[i].name.decode()
+        d["precision"] = "c128" if arr[i].precision == C128 else "c64"
+        out.append(d)
+    return out, tot.value
+
+
+def launch_count():
+    tot = c_int64()
+    _check(load().vie_profile_read(None, 0, None, byref(tot)))
+    return tot.value
 
 
 def _stream():
@@ -135,6 +169,12 @@ class Spectrum:
         if self.handle:
             _check(load().vie_spectrum_release(self.handle))
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
 
 
 class Grid:
