@@ -225,7 +225,9 @@ def main():
 
     for _ in range(args.warmup):
         _, st = g.solve(sp, einc, e, **opts)
-    sampler = ClockSampler(local)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    uuid = str(getattr(props, "uuid", "") or "")
+    sampler = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or local))
     if not args.no_profile:
         vie.profile_enable(True)
     launches0 = vie.launch_count()

@@ -76,8 +76,19 @@ typedef struct {
                                 block-diagonal preconditioner, -1 = no block
                                 (identity); any non-negative ids; NULL = all -1;
                                 copied                                               */
-    uint32_t flags;          /* reserved, must be 0                                  */
+    uint32_t flags;          /* 0 or one VIE_GRID_INNER_* value                      */
 } vie_grid_desc;
+
+/* How the inner block solves of the preconditioner run (vie_grid_desc.flags).
+ * AUTO: a persistent kernel in which each CTA solves whole blocks on its own
+ * for groups of at least 32 blocks whose padded (x, y) plane fits in shared
+ * memory; batched multi-CTA launches per BiCGSTAB step otherwise. The two
+ * paths compute the same iterations; the flags force one of them. */
+enum vie_grid_flags {
+    VIE_GRID_INNER_AUTO = 0,
+    VIE_GRID_INNER_BATCHED = 1,
+    VIE_GRID_INNER_PERSISTENT = 2
+};
 
 typedef struct {
     int32_t nblocks;         /* non-empty blocks found in block_id                 */
@@ -185,7 +196,7 @@ int vie_solve(vie_grid* grid, const vie_spectrum* spectrum, const void* einc_dev
 /* Kernel-level profile, aggregated per kernel kind and precision. */
 typedef struct {
     char name[32];           /* x_fwd, y_fwd, z_green, y_inv, x_inv, bicg_update,
-                                bicg_dot, spectrum, field                          */
+                                bicg_dot, spectrum, field, inner_block             */
     int32_t precision;       /* VIE_C128 or VIE_C64                                 */
     int64_t launches;        /* launches recorded                                   */
     double total_ms;         /* sum of CUDA-event durations, each measured on the

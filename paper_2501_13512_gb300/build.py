@@ -12,8 +12,9 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["fft.cu", "krylov.cu", "fields.cu", "api.cu", "profile.cu"]
-HEADERS = [os.path.join(CSRC, "vie_internal.cuh"), os.path.join(ROOT, "include", "vie.h")]
+SOURCES = ["fft.cu", "krylov.cu", "fields.cu", "api.cu", "profile.cu", "inner.cu"]
+HEADERS = [os.path.join(CSRC, "vie_internal.cuh"), os.path.join(CSRC, "fft_core.cuh"),
+           os.path.join(ROOT, "include", "vie.h")]
 LIB = os.path.join(HERE, "libvie.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",

@@ -202,7 +202,7 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
         return fail(VIE_EINVAL, "vie_grid_create: each of nx, ny, nz must be in [1, 512]");
     if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(VIE_EINVAL, "vie_grid_create: h must be positive");
     if (!d->eps_r) return fail(VIE_EINVAL, "vie_grid_create: eps_r is null");
-    if (d->flags != 0) return fail(VIE_EINVAL, "vie_grid_create: flags must be 0");
+    if (d->flags > VIE_GRID_INNER_PERSISTENT) return fail(VIE_EINVAL, "vie_grid_create: unknown flags");
 
     vie_grid* g = new vie_grid();
     auto bail = [&](int rc) { release_grid(g); return rc; };
@@ -305,6 +305,36 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
         if ((rc = dalloc(g, &gr.st, gr.bs.nb))) return bail(rc);
         if ((rc = alloc_reduce(g, gr.red, gr.bs.nb))) return bail(rc);
         ++gi;
+    }
+    // persistent block solver: eligible groups and their work lists, largest boxes first
+    for (int prec = 0; prec < 2; ++prec) {
+        const size_t es = prec == 0 ? 16 : 8;
+        std::vector<std::pair<int64_t, int2>> items;
+        int job = 0;
+        for (auto& gr : g->groups) {
+            bool ok = d->flags != VIE_GRID_INNER_BATCHED && inner_persistent_ok(gr.bs, es, d->flags == VIE_GRID_INNER_PERSISTENT);
+            (prec == 0 ? gr.persistent128 : gr.persistent64) = ok;
+            if (!ok) continue;
+            for (int b = 0; b < gr.bs.nb; ++b) items.push_back({gr.bs.spec_elems(), make_int2(job, b)});
+            ++job;
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const std::pair<int64_t, int2>& a, const std::pair<int64_t, int2>& b) { return a.first > b.first; });
+        std::vector<int2> w;
+        for (auto& it : items) w.push_back(it.second);
+        int2** dst = prec == 0 ? &g->work128 : &g->work64;
+        (prec == 0 ? g->nwork128 : g->nwork64) = (int)w.size();
+        if (!w.empty()) {
+            if ((rc = dalloc(g, dst, (int64_t)w.size()))) return bail(rc);
+            if (cudaMemcpy(*dst, w.data(), w.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(VIE_ECUDA, "upload of the block work list failed"));
+        }
+    }
+    if (!g->groups.empty()) {
+        char* descs = nullptr;
+        if ((rc = dalloc(g, &descs, (int64_t)(g->groups.size() * inner_group_desc_bytes())))) return bail(rc);
+        g->inner_groups = descs;
+        if ((rc = dalloc(g, &g->inner_next, 1))) return bail(rc);
     }
     if ((rc = dalloc(g, &g->block_id, N))) return bail(rc);
     if (cudaMemcpy(g->block_id, bid.data(), N * 4, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -425,6 +455,9 @@ template <> const float2* spec_of<float2>(const vie_spectrum* sp, int idx) { ret
 template <class C> static KrylovVecs<C>& group_vecs(Group& gr);
 template <> KrylovVecs<double2>& group_vecs<double2>(Group& gr) { return gr.k128; }
 template <> KrylovVecs<float2>& group_vecs<float2>(Group& gr) { return gr.k64; }
+template <class C> static const C* chi_of(const BoxSet& bs);
+template <> const double2* chi_of<double2>(const BoxSet& bs) { return bs.chi128; }
+template <> const float2* chi_of<float2>(const BoxSet& bs) { return bs.chi64; }
 template <class C> static int prec_of();
 template <> int prec_of<double2>() { return VIE_C128; }
 template <> int prec_of<float2>() { return VIE_C64; }
@@ -456,11 +489,31 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     if (stats) memset(stats, 0, sizeof(*stats));
     if (g->nblocks == 0) return vec_copy<C>(b, y, n3, s);
     const int ng = (int)g->groups.size();
-    std::vector<Bicg<C>> bk(ng);
+    const bool c128 = prec_of<C>() == VIE_C128;
+    std::vector<InnerJob<C>> jobs;
+    std::vector<int> batched;
     for (int i = 0; i < ng; ++i) {
         Group& gr = g->groups[i];
         KrylovVecs<C>& v = group_vecs<C>(gr);
         VIE_TRY(precond_gather<C>(g, gr, b, v.b, s));
+        if (c128 ? gr.persistent128 : gr.persistent64) {
+            InnerJob<C> j;
+            j.bs = &gr.bs;
+            j.v = v;
+            j.chi = chi_of<C>(gr.bs);
+            j.G = spec_of<C>(sp, 1 + i);
+            j.st = gr.st;
+            jobs.push_back(j);
+        } else {
+            batched.push_back(i);
+        }
+    }
+    VIE_TRY(inner_persistent<C>(jobs, c128 ? g->work128 : g->work64, c128 ? g->nwork128 : g->nwork64,
+                                g->inner_groups, g->inner_next, tol, maxit, s));
+    std::vector<Bicg<C>> bk(ng);
+    for (int i : batched) {
+        Group& gr = g->groups[i];
+        KrylovVecs<C>& v = group_vecs<C>(gr);
         bk[i].nseg = gr.bs.nb;
         bk[i].seglen = gr.bs.vec_elems();
         bk[i].v = v;
@@ -469,9 +522,9 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
         VIE_TRY(bicg_init<C>(bk[i], tol, maxit, s));
     }
     int* ring = (int*)g->h_ring;
-    for (int it = 0; it < maxit; ++it) {
+    for (int it = 0; it < maxit && !batched.empty(); ++it) {
         const int slot = it & 1;
-        for (int i = 0; i < ng; ++i) {
+        for (int i : batched) {
             Group& gr = g->groups[i];
             Bicg<C>& k = bk[i];
             const C* G = spec_of<C>(sp, 1 + i);
@@ -492,7 +545,7 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             const int prev = slot ^ 1;
             VIE_TRY(wait_event(g->ev[prev], timeout_ms));
             int active = 0;
-            for (int i = 0; i < ng; ++i) active += ring[prev * (ng + 1) + i];
+            for (int i : batched) active += ring[prev * (ng + 1) + i];
             if (active == 0) break;
         }
     }

@@ -39,7 +39,7 @@ Profiler& prof() {
 std::atomic<long long> g_launches{0};
 
 const char* kKindNames[PK_COUNT] = {"x_fwd", "y_fwd", "z_green", "y_inv", "x_inv",
-                                    "bicg_update", "bicg_dot", "spectrum", "field"};
+                                    "bicg_update", "bicg_dot", "spectrum", "field", "inner_block"};
 
 cudaEvent_t take_event(Profiler& p) {
     if (!p.pool.empty()) {

@@ -122,6 +122,8 @@ struct ReduceScratch {
 constexpr int kMaxCtaPerSeg = 256;
 
 struct Group {
+    bool persistent128 = false;        // solved by the persistent block solver
+    bool persistent64 = false;
     BoxSet bs;
     KrylovVecs<double2> k128;
     KrylovVecs<float2> k64;
@@ -163,6 +165,12 @@ struct vie_grid {
     double* dscal = nullptr;              // device scalars: [0] ||b||^2, [1] ||r||^2
     char* h_ring = nullptr;               // pinned host: active counts, state, scalar
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    // persistent block solver: work lists (job, box), largest boxes first
+    int2* work128 = nullptr;
+    int2* work64 = nullptr;
+    int nwork128 = 0, nwork64 = 0;
+    void* inner_groups = nullptr;         // device copy of the per-group descriptors
+    int* inner_next = nullptr;            // work counter
     int64_t device_bytes = 0;
     std::vector<void*> allocations;
 };
@@ -178,7 +186,7 @@ namespace vie {
 // are counted exactly: bytes = units * bytes_per_unit + (units ? fixed : 0).
 enum ProfKind {
     PK_X_FWD = 0, PK_Y_FWD, PK_Z_GREEN, PK_Y_INV, PK_X_INV,
-    PK_BICG_UPDATE, PK_BICG_DOT, PK_SPECTRUM, PK_FIELD, PK_COUNT
+    PK_BICG_UPDATE, PK_BICG_DOT, PK_SPECTRUM, PK_FIELD, PK_INNER, PK_COUNT
 };
 int* prof_begin(cudaStream_t s, int kind, int precision, int64_t bytes_per_unit, int64_t bytes_fixed,
                 bool device_units);
@@ -222,6 +230,24 @@ int vec_residual128(const double2* b, const double2* ax, double2* r, int64_t n, 
 int vec_norm2_128(const double2* a, int64_t n, ReduceScratch* red, double* d_out, cudaStream_t s);
 int vec_scale_to_c64(const double2* a, const double* d_norm2, float2* b, int64_t n, cudaStream_t s);
 int vec_add_scaled_c64(double2* x, const float2* d, const double* d_norm2, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------- inner.cu (persistent block solver)
+constexpr int kInnerMinBlocks = 32;     // fewer blocks than this: batched multi-CTA path instead
+template <class C> struct InnerJob {
+    const BoxSet* bs;
+    KrylovVecs<C> v;
+    const C* chi;
+    const C* G;
+    SegState* st;
+};
+bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force);
+size_t inner_group_desc_bytes();
+template <class C>
+int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, int nwork, void* d_groups,
+                     int* d_next, double tol, int maxit, cudaStream_t s);
+template <class C> inline const C* tw_of(const Twiddles& t);
+template <> inline const double2* tw_of<double2>(const Twiddles& t) { return t.d128; }
+template <> inline const float2* tw_of<float2>(const Twiddles& t) { return t.d64; }
 
 // ---------------------------------------------------------------- precond.cu
 template <class C>

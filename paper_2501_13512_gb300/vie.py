@@ -22,6 +22,7 @@ VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA, VIE_ENOTCONV, VIE_EBREAKDOWN, VIE_ETI
 STATUS_NAMES = {0: "VIE_OK", 1: "VIE_EINVAL", 2: "VIE_ENOMEM", 3: "VIE_ECUDA", 4: "VIE_ENOTCONV",
                 5: "VIE_EBREAKDOWN", 6: "VIE_ETIMEOUT", 7: "VIE_EBUSY"}
 C128, C64 = 1, 2
+INNER_AUTO, INNER_BATCHED, INNER_PERSISTENT = 0, 1, 2
 MODE_PLAIN_C128, MODE_MIXED = 0, 1
 
 
@@ -180,7 +181,7 @@ class Spectrum:
 class Grid:
     """A voxel grid with its contrast and block partition (vie_grid)."""
 
-    def __init__(self, eps_r, h, block_id=None):
+    def __init__(self, eps_r, h, block_id=None, inner=INNER_AUTO):
         lib = load()
         eps_r = np.ascontiguousarray(eps_r, dtype=np.complex128)
         nz, ny, nx = eps_r.shape
@@ -190,14 +191,14 @@ class Grid:
         self._eps = eps_r.view(np.float64).reshape(-1)
         self._bid = None if block_id is None else np.ascontiguousarray(block_id, dtype=np.int32).reshape(-1)
         d = GridDesc(nx, ny, nz, self.h, self._eps.ctypes.data_as(POINTER(c_double)),
-                     None if self._bid is None else self._bid.ctypes.data_as(POINTER(c_int32)), 0)
+                     None if self._bid is None else self._bid.ctypes.data_as(POINTER(c_int32)), int(inner))
         handle = c_void_p()
         _check(lib.vie_grid_create(byref(d), byref(handle)))
         self.handle = handle
 
     @classmethod
-    def from_workload(cls, w):
-        return cls(w.eps_r, w.h, w.block_id if w.use_precond else None)
+    def from_workload(cls, w, inner=INNER_AUTO):
+        return cls(w.eps_r, w.h, w.block_id if w.use_precond else None, inner)
 
     def info(self):
         inf = GridInfo()

@@ -94,11 +94,15 @@ def test_plane_wave():
     assert rel(host(g.plane_wave(K0, khat, pol, precision=vie.C64)), ref) <= 1e-6
 
 
-def test_precond_tight_matches_oracle():
+INNER_PATHS = [vie.INNER_BATCHED, vie.INNER_PERSISTENT]
+
+
+@pytest.mark.parametrize("inner", INNER_PATHS)
+def test_precond_tight_matches_oracle(inner):
     eps_r, bid, b = inputs.random_case((12, 10, 8), seed=31, block_grid=(4, 5, 4))
     P = oprecond.BlockPreconditioner(eps_r, bid, H, K0, inner_tol=1e-12, inner_maxit=300)
     ref = P(b)
-    g = vie.Grid(eps_r, H, bid)
+    g = vie.Grid(eps_r, H, bid, inner=inner)
     sp = g.spectrum(K0)
     y, st = g.precond(sp, dev(b), inner_tol=1e-12, inner_maxit=300)
     assert st["nblocks"] == len(P.blocks)
@@ -106,11 +110,12 @@ def test_precond_tight_matches_oracle():
     assert rel(host(y), ref) <= 1e-9
 
 
+@pytest.mark.parametrize("inner", INNER_PATHS)
 @pytest.mark.parametrize("precision", [vie.C128, vie.C64])
-def test_precond_loose_meets_inner_tolerance(precision):
+def test_precond_loose_meets_inner_tolerance(precision, inner):
     # uneven blocks (ragged at the grid edge) solved to 1e-2: each block's own residual meets it
     eps_r, bid, b = inputs.random_case((13, 11, 7), seed=17, block_grid=(5, 4, 7))
-    g = vie.Grid(eps_r, H, bid)
+    g = vie.Grid(eps_r, H, bid, inner=inner)
     sp = g.spectrum(K0)
     dt = torch.complex128 if precision == vie.C128 else torch.complex64
     y, st = g.precond(sp, dev(b, dt), inner_tol=1e-2, inner_maxit=100)
@@ -124,6 +129,26 @@ def test_precond_loose_meets_inner_tolerance(precision):
         assert np.linalg.norm(bk - op(xk)) <= 1.01e-2 * np.linalg.norm(bk)
     air = bid < 0
     assert np.array_equal(y[:, air], bb[:, air])
+
+
+@pytest.mark.parametrize("precision", [vie.C128, vie.C64])
+def test_precond_paths_agree_on_metasurface_blocks(precision):
+    # the two inner-solver paths run the same recurrences with different rounding
+    # orders (2D plane FFTs vs pencil passes): results agree to the inner tolerance
+    w = inputs.metasurface(cells=4, seed=3)
+    rng = np.random.default_rng(2)
+    b = rng.normal(size=(3,) + w.eps_r.shape) + 1j * rng.normal(size=(3,) + w.eps_r.shape)
+    dt = torch.complex128 if precision == vie.C128 else torch.complex64
+    itol = 1e-6 if precision == vie.C128 else 1e-4     # FP32 stalls near 1e-6
+    out = []
+    for inner in INNER_PATHS:
+        g = vie.Grid.from_workload(w, inner=inner)
+        sp = g.spectrum(w.k0)
+        y, st = g.precond(sp, dev(b, dt), inner_tol=itol, inner_maxit=200)
+        assert st["nblocks"] == 16 and st["not_converged"] == 0
+        out.append((host(y), st))
+    assert rel(out[1][0], out[0][0]) <= 10 * itol
+    assert abs(out[0][1]["mean_iters"] - out[1][1]["mean_iters"]) <= 1.0
 
 
 def test_precond_without_blocks_is_identity():
