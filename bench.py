@@ -38,11 +38,12 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "metasurface_reference.json")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plain-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--plain-iters", type=int, default=3,
+                    help="outer iterations of the plain FP64 solve to time (it needs hundreds to converge)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     return ap.parse_args()
@@ -102,7 +103,7 @@ def outer_iters_reference(default):
     if os.path.exists(GOLDEN):
         with open(GOLDEN) as f:
             return float(json.load(f)["outer_iters"]), "oracle full solve (tests/golden/metasurface_reference.json)"
-    return float(default), "plain FP64 GPU solve (same recurrences as the oracle)"
+    return float(default), "GPU mixed solve of the same workload (oracle full-solve count not yet recorded)"
 
 
 def run_reference(args, rank):
@@ -276,24 +277,26 @@ def main():
     mvm64 = time_mvm(vie.C64, 20)
     mvm128 = time_mvm(vie.C128, 5)
 
-    # plain FP64 solve of the same problem
+    # plain FP64 solve of the same problem: time a bounded number of outer iterations
     plain = None
-    if args.plain_steps > 0:
-        pl = []
+    if args.plain_iters > 0:
         e_plain = g.empty()
-        for _ in range(args.plain_steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            _, pst = g.solve(sp, einc, e_plain, outer_tol=w.outer_tol, inner_tol=w.inner_tol, use_precond=True,
-                             mode=vie.MODE_PLAIN_C128)
-            b.record(stream)
-            torch.cuda.synchronize()
-            pl.append(a.elapsed_time(b))
-        diff = float(torch.linalg.vector_norm(e_mixed - e_plain) / torch.linalg.vector_norm(e_plain))
-        plain = {"solves_per_s": 1e3 / float(np.mean(pl)), "ms": float(np.mean(pl)),
-                 "outer_iters": pst["outer_iters"], "true_rel_res": pst["true_rel_res"],
-                 "matvecs_c128": pst["matvecs_c128"], "inner_iters": pst["inner_iters"],
-                 "mixed_vs_plain_rel_field_diff": diff}
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, pst = g.solve(sp, einc, e_plain, outer_tol=w.outer_tol, inner_tol=w.inner_tol, use_precond=True,
+                         mode=vie.MODE_PLAIN_C128, outer_maxit=args.plain_iters, check=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        mixed_ms_iter = elapsed * 1e3 / args.steps / max(1.0, stats[-1]["outer_iters"])
+        plain = {"outer_iters_timed": pst["outer_iters"], "ms": ms,
+                 "ms_per_outer_iter": ms / max(1.0, pst["outer_iters"]),
+                 "mixed_ms_per_outer_iter": mixed_ms_iter,
+                 "true_rel_res_after": pst["true_rel_res"],
+                 "solves_per_s_est": 1e3 / (ms / max(1.0, pst["outer_iters"]) * stats[-1]["outer_iters"]),
+                 "note": "plain complex128 BiCGSTAB with complex128 block solves; it does not reach 1e-6 in "
+                         "150 outer iterations on this workload, so a bounded number of iterations is timed and "
+                         "solves_per_s_est assumes the mixed solve's outer-iteration count (optimistic)"}
 
     # field error against the oracle's full solve at seeded sample voxels
     accuracy = None
@@ -319,6 +322,26 @@ def main():
         e2e = {"value": args.e2e_steps / (t1 - t0), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
 
+    # full-grid MVM pass kernels, profiled separately (HBM-streaming FFT passes)
+    roof_mvm = None
+    if not args.no_profile:
+        x64 = einc.to(torch.complex64)
+        y64 = g.empty(vie.C64)
+        g.matvec(sp, x64, y64)
+        vie.profile_enable(True)
+        for _ in range(10):
+            g.matvec(sp, x64, y64)
+        mk, _ = vie.profile_read()
+        vie.profile_enable(False)
+        peak0, src0 = peaks()
+        dm = max(mk, key=lambda k: k["total_ms"])
+        ach = dm["bytes"] / (dm["total_ms"] * 1e-3) / 1e9
+        roof_mvm = {"bound": "hbm", "kernel": f"{dm['name']}_{dm['precision']}", "achieved": ach, "peak": peak0,
+                    "unit": "GB/s", "frac": ach / peak0, "ms_per_launch": dm["total_ms"] / dm["launches"],
+                    "algorithmic_bytes_per_launch": dm["bytes"] / dm["launches"],
+                    "passes": {f"{k['name']}_{k['precision']}": round(k["bytes"] / (k["total_ms"] * 1e-3) / 1e9, 1)
+                               for k in mk}}
+
     # roofline of the dominant kernel kind over the timed region
     peak, peak_src = peaks()
     roof = None
@@ -341,7 +364,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        iters, src = outer_iters_reference(plain["outer_iters"] if plain else 20)
+        iters, src = outer_iters_reference(stats[-1]["outer_iters"])
         s = OracleSample(w, block_stride=4).run()
         v = 1.0 / (s["t_iter"] * iters)
         cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -360,7 +383,8 @@ def main():
                       "matvecs_c64": last["matvecs_c64"], "refinements": last["refinements"],
                       "true_rel_res": last["true_rel_res"]},
             "plain_c128": plain, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches,
-            "roofline": roof, "kernels": kernels, "clocks": clocks, "cpu_baseline": cpu}
+            "roofline": roof, "roofline_full_grid_mvm": roof_mvm, "kernels": kernels, "clocks": clocks,
+            "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

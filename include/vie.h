@@ -80,9 +80,10 @@ typedef struct {
 } vie_grid_desc;
 
 /* How the inner block solves of the preconditioner run (vie_grid_desc.flags).
- * AUTO: a persistent kernel in which each CTA solves whole blocks on its own
- * for groups of at least 32 blocks whose padded (x, y) plane fits in shared
- * memory; batched multi-CTA launches per BiCGSTAB step otherwise. The two
+ * AUTO: a persistent kernel in which each CTA solves whole blocks on its own,
+ * for every group whose padded (x, y) plane fits in shared memory, when those
+ * groups hold at least 32 blocks together; batched multi-CTA launches per
+ * BiCGSTAB step otherwise. The two
  * paths compute the same iterations; the flags force one of them. */
 enum vie_grid_flags {
     VIE_GRID_INNER_AUTO = 0,

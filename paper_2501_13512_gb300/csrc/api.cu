@@ -311,8 +311,14 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
         const size_t es = prec == 0 ? 16 : 8;
         std::vector<std::pair<int64_t, int2>> items;
         int job = 0;
+        // AUTO: every group whose plane fits joins one persistent launch when the
+        // fitting groups hold at least kInnerMinBlocks blocks in total
+        int fit_blocks = 0;
+        for (auto& gr : g->groups)
+            if (inner_persistent_ok(gr.bs, es, true)) fit_blocks += gr.bs.nb;
+        const bool force = d->flags == VIE_GRID_INNER_PERSISTENT || fit_blocks >= kInnerMinBlocks;
         for (auto& gr : g->groups) {
-            bool ok = d->flags != VIE_GRID_INNER_BATCHED && inner_persistent_ok(gr.bs, es, d->flags == VIE_GRID_INNER_PERSISTENT);
+            bool ok = d->flags != VIE_GRID_INNER_BATCHED && inner_persistent_ok(gr.bs, es, force);
             (prec == 0 ? gr.persistent128 : gr.persistent64) = ok;
             if (!ok) continue;
             for (int b = 0; b < gr.bs.nb; ++b) items.push_back({gr.bs.spec_elems(), make_int2(job, b)});

@@ -24,6 +24,7 @@ namespace vie {
 
 template <class C> struct InnerGroup {
     C *b, *x, *r, *rhat, *p, *v, *s, *t;   // [nb][3][bz][by][bx]
+    C* w1;                                  // [nb][3][bz][by][Mx] (register path)
     C* w2;                                  // [nb][3][bz][My][Mx]
     const C* chi;                           // [nb][bz][by][bx]
     const uint8_t* mask;                    // [nb][bz][by][bx]
@@ -34,6 +35,7 @@ template <class C> struct InnerGroup {
     int ltc;                                // log2 columns per Z tile
     int kb_mvm;                             // profiling: KB moved by one MVM and its fused updates
     int kb_upd;                             // profiling: KB moved by the x/r update pass
+    int reg;                                // 1: register-FFT MVM (complex64, every padded axis <= 32)
 };
 
 constexpr int kInnerThreads = 256;
@@ -213,27 +215,437 @@ __device__ void phase_xy_inv(const InnerGroup<C>& g, int64_t voff, const C* W, c
     cta_sum2(d1, d2, red);
 }
 
-template <class C>
-__device__ void solve_block(const InnerGroup<C>& g, int b, double tol, int maxit, C* sm, const C* tw,
+// ---------------------------------------------------------------- register-FFT box MVM (complex64)
+// Radix-2 FFT of one pencil held in registers, fully unrolled. FWD: natural
+// order in, bit-reversed out (decimation in frequency); !FWD: bit-reversed in,
+// natural out, unnormalised (decimation in time). Same ordering as the
+// shared-memory passes, so spectra from either path are interchangeable.
+template <bool FWD, class C>
+__device__ __forceinline__ C twmul(C v, int m, const C* __restrict__ tw) {
+    if (m == 0) return v;
+    if (m == kLmax / 4) return FWD ? mul_mi(v) : mul_i(v);
+    C w = __ldg(&tw[m]);
+    return FWD ? cmul(v, w) : cmulc(v, w);
+}
+
+// One radix-2 stage of span S (a compile-time constant) on an L-point pencil.
+template <int L, int S, bool FWD, class C>
+__device__ __forceinline__ void rstage(C (&a)[L], const C* __restrict__ tw) {
+#pragma unroll
+    for (int g = 0; g < L; g += 2 * S) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const int m = j * (kLmax / (2 * S));
+            if (FWD) {
+                C x0 = a[g + j], x1 = a[g + j + S];
+                a[g + j] = x0 + x1;
+                a[g + j + S] = twmul<true>(x0 - x1, m, tw);
+            } else {
+                C x0 = a[g + j], x1 = twmul<false>(a[g + j + S], m, tw);
+                a[g + j] = x0 + x1;
+                a[g + j + S] = x0 - x1;
+            }
+        }
+    }
+}
+
+// Stages with spans S, S/2, ..., 1 (forward) or S, 2S, ..., L/2 (inverse).
+template <int L, int S, bool FWD> struct RStages {
+    template <class C> static __device__ __forceinline__ void run(C (&a)[L], const C* __restrict__ tw) {
+        rstage<L, S, FWD>(a, tw);
+        RStages<L, FWD ? S / 2 : S * 2, FWD>::run(a, tw);
+    }
+};
+template <int L> struct RStages<L, 0, true> {
+    template <class C> static __device__ __forceinline__ void run(C (&)[L], const C* __restrict__) {}
+};
+template <int L> struct RStages<L, L, false> {
+    template <class C> static __device__ __forceinline__ void run(C (&)[L], const C* __restrict__) {}
+};
+
+template <int L, bool FWD, class C>
+__device__ __forceinline__ void rfft(C (&a)[L], const C* __restrict__ tw) {
+    if (L < 2) return;
+    RStages<L, FWD ? L / 2 : 1, FWD>::run(a, tw);
+}
+
+typedef float2 F;
+constexpr int kU = 1;   // elements per thread whose loads are issued together (1: lowest register use)
+
+// Pruned transforms. A box of b voxels is padded to L >= 2b - 1, a power of
+// two, so b <= L/2: forward inputs beyond L/2 are zero and inverse outputs
+// beyond L/2 are discarded. The first DIF stage then splits the L-point
+// transform into FFT_{L/2}(x) (positions [0, L/2)) and FFT_{L/2}(x_j W_L^j)
+// (positions [L/2, L)); the last DIT stage of the inverse combines
+// u = iFFT_{L/2}(lower half) and v = iFFT_{L/2}(upper half) as
+// u_j + conj(W_L^j) v_j. Only L/2 values are live in registers at a time.
+
+// Forward: get(j) gives input j < L/2 (zero where the box ends); put(k, v)
+// receives output position k (bit-reversed order).
+template <int L, class Get, class Put>
+__device__ __forceinline__ void fwd_half(Get get, Put put, const F* __restrict__ tw) {
+    if (L == 1) {
+        put(0, get(0));
+        return;
+    }
+    constexpr int H = L / 2 > 0 ? L / 2 : 1;
+    F a[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) a[j] = twmul<true>(get(j), j * (kLmax / L), tw);
+    rfft<H, true>(a, tw);
+#pragma unroll
+    for (int j = 0; j < H; ++j) put(H + j, a[j]);
+#pragma unroll
+    for (int j = 0; j < H; ++j) a[j] = get(j);
+    rfft<H, true>(a, tw);
+#pragma unroll
+    for (int j = 0; j < H; ++j) put(j, a[j]);
+}
+
+// Inverse keeping outputs [0, L/2): get(k) gives input position k;
+// stash(j, v) / unstash(j) hold conj(W_L^j) v_j between the two halves;
+// put(j, v) receives output j (called for every j < L/2).
+template <int L, class Get, class Stash, class Unstash, class Put>
+__device__ __forceinline__ void inv_half(Get get, Stash stash, Unstash unstash, Put put, const F* __restrict__ tw) {
+    if (L == 1) {
+        put(0, get(0));
+        return;
+    }
+    constexpr int H = L / 2 > 0 ? L / 2 : 1;
+    F a[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) a[j] = get(H + j);
+    rfft<H, false>(a, tw);
+#pragma unroll
+    for (int j = 0; j < H; ++j) stash(j, twmul<false>(a[j], j * (kLmax / L), tw));
+#pragma unroll
+    for (int j = 0; j < H; ++j) a[j] = get(j);
+    rfft<H, false>(a, tw);
+#pragma unroll
+    for (int j = 0; j < H; ++j) put(j, a[j] + unstash(j));
+}
+
+// X forward: rows (component, z, y) of the box. Coalesced loads (with the
+// BiCGSTAB update fused) into IN, one pruned row FFT per thread into OUT,
+// coalesced stores of OUT to W1. Shared memory: T (bx + 1) + T (LX + 1).
+template <int LX, int IN>
+__device__ __forceinline__ F x_fwd_reg(const InnerGroup<F>& g, int64_t voff, F* W1, const F* chi, F* sm,
+                                       const F* tw, F c1, F c2) {
+    const int R = 3 * g.bz * g.by, bx = g.bx, plane = g.bz * g.by, T = blockDim.x, t = threadIdx.x;
+    F* smi = sm;
+    F* smo = sm + T * (bx + 1);
+    F acc = czero<F>();
+    for (int r0 = 0; r0 < R; r0 += T) {
+        const int nr = min(T, R - r0);
+        const int64_t base = voff + (int64_t)r0 * bx;
+        const int nk = nr * bx;
+        for (int k0 = t; k0 < nk; k0 += kU * T) {
+            F ra[kU], pa[kU], va[kU], ca[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {          // all loads of the batch first
+                const int k = k0 + u * T;
+                if (k < nk) {
+                    const int64_t e = base + k;
+                    const int rr = k / bx, x = k - rr * bx;
+                    ra[u] = g.r[e];
+                    va[u] = g.v[e];
+                    if (IN == IN_P) pa[u] = g.p[e];
+                    ca[u] = chi[(int64_t)((r0 + rr) % plane) * bx + x];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int k = k0 + u * T;
+                if (k < nk) {
+                    const int64_t e = base + k;
+                    const int rr = k / bx, x = k - rr * bx;
+                    F in;
+                    if (IN == IN_P) {
+                        in = ra[u] + cmul(c1, pa[u] - cmul(c2, va[u]));
+                        g.p[e] = in;
+                    } else {
+                        in = ra[u] - cmul(c1, va[u]);
+                        g.s[e] = in;
+                        acc.x += in.x * in.x + in.y * in.y;
+                    }
+                    smi[rr * (bx + 1) + x] = cmul(in, ca[u]);
+                }
+            }
+        }
+        __syncthreads();
+        if (t < nr) {
+            const F* row = smi + t * (bx + 1);
+            F* out = smo + t * (LX + 1);
+            fwd_half<LX>([&](int j) { return j < bx ? row[j] : czero<F>(); }, [&](int k, F v) { out[k] = v; }, tw);
+        }
+        __syncthreads();
+        F* dst = W1 + (int64_t)r0 * LX;
+        for (int k = t; k < nr * LX; k += T) dst[k] = smo[(k / LX) * (LX + 1) + (k & (LX - 1))];
+        __syncthreads();
+    }
+    return acc;
+}
+
+// Y forward: one column (component, z, x) per thread, straight from W1 (coalesced along x).
+template <int LY>
+__device__ __forceinline__ void y_fwd_reg(const InnerGroup<F>& g, const F* W1, F* W2, const F* tw) {
+    const int LX = g.Mx, cols = 3 * g.bz * LX, by = g.by;
+    for (int col = threadIdx.x; col < cols; col += blockDim.x) {
+        int pz = col / LX, x = col - pz * LX;
+        const F* src = W1 + (int64_t)pz * by * LX + x;
+        F* dst = W2 + (int64_t)pz * LY * LX + x;
+        fwd_half<LY>([&](int j) { return j < by ? src[j * LX] : czero<F>(); }, [&](int k, F v) { dst[k * LX] = v; },
+                     tw);
+    }
+}
+
+// Y inverse: one column per thread, keep y < by; the stash lives in W1's column.
+template <int LY>
+__device__ __forceinline__ void y_inv_reg(const InnerGroup<F>& g, const F* W2, F* W1, const F* tw) {
+    const int LX = g.Mx, cols = 3 * g.bz * LX, by = g.by;
+    for (int col = threadIdx.x; col < cols; col += blockDim.x) {
+        int pz = col / LX, x = col - pz * LX;
+        const F* src = W2 + (int64_t)pz * LY * LX + x;
+        F* dst = W1 + (int64_t)pz * by * LX + x;
+        inv_half<LY>([&](int k) { return src[k * LX]; },
+                     [&](int j, F v) { if (j < by) dst[j * LX] = v; },
+                     [&](int j) { return j < by ? dst[j * LX] : czero<F>(); },
+                     [&](int j, F v) { if (j < by) dst[j * LX] = v; }, tw);
+    }
+}
+
+constexpr int kZCols = 128;   // spectral columns per Z round
+
+// Z: forward along z, 3x3 Green multiply, inverse, keep z < bz. Per round the
+// three transformed components of kZCols columns are staged in shared memory.
+// Offsets are 32-bit (a padded plane has at most 2^20 points).
+template <int LZ>
+__device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, const F* tw) {
+    constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1;
+    const int P = g.My * g.Mx, T = blockDim.x, t = threadIdx.x, bz = g.bz;
+    const int cs = bz * P, gc = LZ * P;
+    for (int c0 = 0; c0 < P; c0 += kZCols) {
+        const int nc = min(kZCols, P - c0);
+        for (int task = t; task < 3 * nc; task += T) {
+            const int comp = task / nc, c = task - comp * nc;
+            const F* src = W2 + comp * cs + c0 + c;
+            F* S = sm + comp * LZ * kZCols + c;
+            if (LZ == 1) {
+                S[0] = src[0];
+                continue;
+            }
+            F a[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) a[j] = j < bz ? src[j * P] : czero<F>();
+#pragma unroll
+            for (int j = 0; j < H; ++j) a[j] = twmul<true>(a[j], j * (kLmax / LZ), tw);
+            rfft<H, true>(a, tw);
+#pragma unroll
+            for (int j = 0; j < H; ++j) S[(H + j) * kZCols] = a[j];
+#pragma unroll
+            for (int j = 0; j < H; ++j) a[j] = j < bz ? src[j * P] : czero<F>();
+            rfft<H, true>(a, tw);
+#pragma unroll
+            for (int j = 0; j < H; ++j) S[j * kZCols] = a[j];
+        }
+        __syncthreads();
+        const int cst = LZ * kZCols;
+        for (int task0 = t; task0 < LZ * nc; task0 += kU * T) {
+            F gv[kU][6];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int task = task0 + u * T;
+                if (task < LZ * nc) {
+                    const int i = task / nc, c = task - i * nc;
+                    const F* gp = g.G + i * P + c0 + c;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) gv[u][q] = gp[q * gc];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int task = task0 + u * T;
+                if (task < LZ * nc) {
+                    const int i = task / nc, c = task - i * nc;
+                    F* q = sm + i * kZCols + c;
+                    F X = q[0], Y = q[cst], Z = q[2 * cst];
+                    q[0] = cmul(gv[u][0], X) + cmul(gv[u][1], Y) + cmul(gv[u][2], Z);
+                    q[cst] = cmul(gv[u][1], X) + cmul(gv[u][3], Y) + cmul(gv[u][4], Z);
+                    q[2 * cst] = cmul(gv[u][2], X) + cmul(gv[u][4], Y) + cmul(gv[u][5], Z);
+                }
+            }
+        }
+        __syncthreads();
+        for (int task = t; task < 3 * nc; task += T) {
+            const int comp = task / nc, c = task - comp * nc;
+            F* S = sm + comp * LZ * kZCols + c;
+            F* dst = W2 + comp * cs + c0 + c;
+            if (LZ == 1) {
+                dst[0] = S[0];
+                continue;
+            }
+            F a[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) a[j] = S[(H + j) * kZCols];
+            rfft<H, false>(a, tw);
+#pragma unroll
+            for (int j = 0; j < H; ++j) S[(H + j) * kZCols] = twmul<false>(a[j], j * (kLmax / LZ), tw);
+#pragma unroll
+            for (int j = 0; j < H; ++j) a[j] = S[j * kZCols];
+            rfft<H, false>(a, tw);
+#pragma unroll
+            for (int j = 0; j < H; ++j)
+                if (j < bz) dst[j * P] = a[j] + S[(H + j) * kZCols];
+        }
+        __syncthreads();
+    }
+}
+
+// X inverse: rows of W1, keep x < bx, out = mask (in - u) with the iteration's dots.
+template <int LX, int OUT>
+__device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, const F* W1, const uint8_t* mask,
+                                          F* sm, const F* tw, F& a1, F& a2) {
+    const int R = 3 * g.bz * g.by, bx = g.bx, plane = g.bz * g.by, T = blockDim.x, t = threadIdx.x;
+    F* smi = sm;
+    F* smo = sm + T * (LX + 1);
+    for (int r0 = 0; r0 < R; r0 += T) {
+        const int nr = min(T, R - r0);
+        const F* src = W1 + (int64_t)r0 * LX;
+        for (int k = t; k < nr * LX; k += T) smi[(k / LX) * (LX + 1) + (k & (LX - 1))] = src[k];
+        __syncthreads();
+        if (t < nr) {
+            const F* row = smi + t * (LX + 1);
+            F* out = smo + t * (bx + 1);
+            inv_half<LX>([&](int k) { return row[k]; },
+                         [&](int j, F v) { if (j < bx) out[j] = v; },
+                         [&](int j) { return j < bx ? out[j] : czero<F>(); },
+                         [&](int j, F v) { if (j < bx) out[j] = v; }, tw);
+        }
+        __syncthreads();
+        const int64_t base = voff + (int64_t)r0 * bx;
+        const int nk = nr * bx;
+        for (int k0 = t; k0 < nk; k0 += kU * T) {
+            F ia[kU], ha[kU];
+            uint8_t ma[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int k = k0 + u * T;
+                if (k < nk) {
+                    const int64_t e = base + k;
+                    const int rr = k / bx, x = k - rr * bx;
+                    ia[u] = OUT == OUT_V ? g.p[e] : g.s[e];
+                    if (OUT == OUT_V) ha[u] = g.rhat[e];
+                    ma[u] = mask[(int64_t)((r0 + rr) % plane) * bx + x];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int k = k0 + u * T;
+                if (k < nk) {
+                    const int64_t e = base + k;
+                    const int rr = k / bx, x = k - rr * bx;
+                    F o = ma[u] ? ia[u] - smo[rr * (bx + 1) + x] : czero<F>();
+                    if (OUT == OUT_V) {
+                        g.v[e] = o;
+                        acc_dot(a1, ha[u], o);
+                    } else {
+                        g.t[e] = o;
+                        acc_dot(a1, o, ia[u]);
+                        a2.x += o.x * o.x + o.y * o.y;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+#define VIE_LEN_SWITCH(l, CALL)                                        \
+    switch (l) {                                                       \
+        case 0: { constexpr int LL = 1; CALL; } break;                 \
+        case 1: { constexpr int LL = 2; CALL; } break;                 \
+        case 2: { constexpr int LL = 4; CALL; } break;                 \
+        case 3: { constexpr int LL = 8; CALL; } break;                 \
+        case 4: { constexpr int LL = 16; CALL; } break;                \
+        default: { constexpr int LL = 32; CALL; } break;               \
+    }
+
+// The two MVM implementations used by solve_block.
+template <class C> struct SmemMvm {
+    template <int IN>
+    static __device__ double2 fwd(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const C* chi, C* sm,
+                                  const C* tw, C c1, C c2, double2* red) {
+        return phase_xy<C, IN>(g, voff, W2, chi, sm, tw, c1, c2, red);
+    }
+    static __device__ void mid(const InnerGroup<C>& g, C* W2, C* sm, const C* tw) { phase_z<C>(g, W2, sm, tw); }
+    template <int OUT>
+    static __device__ void inv(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const uint8_t* mask, C* sm,
+                               const C* tw, double2* red, double2& d1, double2& d2) {
+        phase_xy_inv<C, OUT>(g, voff, W2, mask, sm, tw, red, d1, d2);
+    }
+};
+
+struct RegMvm {
+    template <int IN>
+    static __device__ __forceinline__ double2 fwd(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const F* chi, F* sm,
+                                  const F* tw, F c1, F c2, double2* red) {
+        F acc = czero<F>();
+        VIE_LEN_SWITCH(g.lx, (acc = x_fwd_reg<LL, IN>(g, voff, W1, chi, sm, tw, c1, c2)));
+        __syncthreads();
+        VIE_LEN_SWITCH(g.ly, (y_fwd_reg<LL>(g, W1, W2, tw)));
+        double2 a = make_double2(acc.x, acc.y), z = make_double2(0, 0);
+        cta_sum2(a, z, red);   // begins with a barrier, so W2 is complete afterwards
+        return a;
+    }
+    static __device__ __forceinline__ void mid(const InnerGroup<F>& g, F* W2, F* sm, const F* tw) {
+        VIE_LEN_SWITCH(g.lz, (z_reg<LL>(g, W2, sm, tw)));
+    }
+    template <int OUT>
+    static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const uint8_t* mask, F* sm,
+                               const F* tw, double2* red, double2& d1, double2& d2) {
+        VIE_LEN_SWITCH(g.ly, (y_inv_reg<LL>(g, W2, W1, tw)));
+        __syncthreads();
+        F a1 = czero<F>(), a2 = czero<F>();
+        VIE_LEN_SWITCH(g.lx, (x_inv_reg<LL, OUT>(g, voff, W1, mask, sm, tw, a1, a2)));
+        d1 = make_double2(a1.x, a1.y);
+        d2 = make_double2(a2.x, a2.y);
+        cta_sum2(d1, d2, red);
+    }
+};
+
+template <class C, class Mvm>
+__device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, double tol, int maxit, C* sm, const C* tw,
                             double2* red, int* units) {
     const int64_t box = (int64_t)g.bx * g.by * g.bz;
     const int64_t n = 3 * box;
     const int64_t voff = (int64_t)b * n;
     C* W = g.w2 + (int64_t)b * 3 * g.bz * g.My * g.Mx;
+    C* W1 = g.w1 + (int64_t)b * 3 * g.bz * g.by * g.Mx;
     const C* chi = g.chi + (int64_t)b * box;
     const uint8_t* mask = g.mask + (int64_t)b * box;
 
     // x = 0, r = rhat = b, p = v = 0
     C acc = czero<C>();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        int64_t e = voff + i;
-        C bv = g.b[e];
-        g.x[e] = czero<C>();
-        g.r[e] = bv;
-        g.rhat[e] = bv;
-        g.p[e] = czero<C>();
-        g.v[e] = czero<C>();
-        acc.x += bv.x * bv.x + bv.y * bv.y;
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += kU * blockDim.x) {
+        C bv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t i = i0 + u * blockDim.x;
+            if (i < n) bv[u] = g.b[voff + i];
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t i = i0 + u * blockDim.x;
+            if (i < n) {
+                const int64_t e = voff + i;
+                g.x[e] = czero<C>();
+                g.r[e] = bv[u];
+                g.rhat[e] = bv[u];
+                g.p[e] = czero<C>();
+                g.v[e] = czero<C>();
+                acc.x += bv[u].x * bv[u].x + bv[u].y * bv[u].y;
+            }
+        }
     }
     double2 d1 = wide<C>(acc), d2 = make_double2(0, 0);
     cta_sum2(d1, d2, red);
@@ -248,15 +660,15 @@ __device__ void solve_block(const InnerGroup<C>& g, int b, double tol, int maxit
         if (!dgood(rho)) { status = SEG_BREAKDOWN; break; }
         double2 beta = cmul(dcdiv(rho, rho_prev), dcdiv(alpha, omega));
         // v = A p, p = r + beta (p - omega v)
-        phase_xy<C, IN_P>(g, voff, W, chi, sm, tw, cmk<C>(beta.x, beta.y), cmk<C>(omega.x, omega.y), red);
-        phase_z<C>(g, W, sm, tw);
+        Mvm::template fwd<IN_P>(g, voff, W1, W, chi, sm, tw, cmk<C>(beta.x, beta.y), cmk<C>(omega.x, omega.y), red);
+        Mvm::mid(g, W, sm, tw);
         if (units != nullptr && threadIdx.x == 0) atomicAdd(units, g.kb_mvm);
         double2 sigma, unused;
-        phase_xy_inv<C, OUT_V>(g, voff, W, mask, sm, tw, red, sigma, unused);
+        Mvm::template inv<OUT_V>(g, voff, W1, W, mask, sm, tw, red, sigma, unused);
         if (!dgood(sigma)) { status = SEG_BREAKDOWN; break; }
         alpha = dcdiv(rho, sigma);
         // s = r - alpha v, and its transform for t = A s
-        double2 sn = phase_xy<C, IN_S>(g, voff, W, chi, sm, tw, cmk<C>(alpha.x, alpha.y), czero<C>(), red);
+        double2 sn = Mvm::template fwd<IN_S>(g, voff, W1, W, chi, sm, tw, cmk<C>(alpha.x, alpha.y), czero<C>(), red);
         if (sn.x <= tol2) {
             // half-step convergence: x += alpha p
             C ac = cmk<C>(alpha.x, alpha.y);
@@ -269,23 +681,41 @@ __device__ void solve_block(const InnerGroup<C>& g, int b, double tol, int maxit
             status = SEG_CONVERGED;
             break;
         }
-        phase_z<C>(g, W, sm, tw);
+        Mvm::mid(g, W, sm, tw);
         if (units != nullptr && threadIdx.x == 0) atomicAdd(units, g.kb_mvm + g.kb_upd);
         double2 ts, tt;
-        phase_xy_inv<C, OUT_T>(g, voff, W, mask, sm, tw, red, ts, tt);
+        Mvm::template inv<OUT_T>(g, voff, W1, W, mask, sm, tw, red, ts, tt);
         if (!(tt.x > 0.0) || !isfinite(tt.x)) { status = SEG_BREAKDOWN; break; }
         omega = make_double2(ts.x / tt.x, ts.y / tt.x);
         // x += alpha p + omega s, r = s - omega t; rho = <rhat, r>, ||r||^2
         C ac = cmk<C>(alpha.x, alpha.y), oc = cmk<C>(omega.x, omega.y);
         C a1 = czero<C>(), a2 = czero<C>();
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            int64_t e = voff + i;
-            C sv = g.s[e];
-            g.x[e] = g.x[e] + cmul(ac, g.p[e]) + cmul(oc, sv);
-            C rv = sv - cmul(oc, g.t[e]);
-            g.r[e] = rv;
-            acc_dot(a1, g.rhat[e], rv);
-            a2.x += rv.x * rv.x + rv.y * rv.y;
+        for (int64_t i0 = threadIdx.x; i0 < n; i0 += kU * blockDim.x) {
+            C sv[kU], xv[kU], pv[kU], tv[kU], hv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t i = i0 + u * blockDim.x;
+                if (i < n) {
+                    const int64_t e = voff + i;
+                    sv[u] = g.s[e];
+                    xv[u] = g.x[e];
+                    pv[u] = g.p[e];
+                    tv[u] = g.t[e];
+                    hv[u] = g.rhat[e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t i = i0 + u * blockDim.x;
+                if (i < n) {
+                    const int64_t e = voff + i;
+                    g.x[e] = xv[u] + cmul(ac, pv[u]) + cmul(oc, sv[u]);
+                    C rv = sv[u] - cmul(oc, tv[u]);
+                    g.r[e] = rv;
+                    acc_dot(a1, hv[u], rv);
+                    a2.x += rv.x * rv.x + rv.y * rv.y;
+                }
+            }
         }
         d1 = wide<C>(a1);
         d2 = wide<C>(a2);
@@ -310,8 +740,18 @@ __device__ void solve_block(const InnerGroup<C>& g, int b, double tol, int maxit
     __syncthreads();
 }
 
+__device__ __forceinline__ void solve_dispatch(const InnerGroup<double2>& g, int b, double tol, int maxit,
+                                               double2* sm, const double2* tw, double2* red, int* units) {
+    solve_block<double2, SmemMvm<double2>>(g, b, tol, maxit, sm, tw, red, units);
+}
+__device__ __forceinline__ void solve_dispatch(const InnerGroup<float2>& g, int b, double tol, int maxit,
+                                               float2* sm, const float2* tw, double2* red, int* units) {
+    if (g.reg) solve_block<float2, RegMvm>(g, b, tol, maxit, sm, tw, red, units);
+    else solve_block<float2, SmemMvm<float2>>(g, b, tol, maxit, sm, tw, red, units);
+}
+
 template <class C>
-__global__ void __launch_bounds__(kInnerThreads) k_inner(const InnerGroup<C>* groups, const int2* work, int nwork,
+__global__ void __launch_bounds__(kInnerThreads, 2) k_inner(const InnerGroup<C>* groups, const int2* work, int nwork,
                                                           int* next, double tol, int maxit, const C* tw,
                                                           int* units) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -325,7 +765,7 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner(const InnerGroup<C>* gr
         __syncthreads();
         if (it >= nwork) break;
         const int2 wk = work[it];
-        solve_block<C>(groups[wk.x], wk.y, tol, maxit, sm, tw, red, units);
+        solve_dispatch(groups[wk.x], wk.y, tol, maxit, sm, tw, red, units);
     }
 }
 
@@ -355,10 +795,21 @@ static bool inner_tiles(const BoxSet& bs, size_t es, int* lpt, int* ltc, size_t*
     return true;
 }
 
+// Register-FFT MVM: complex64 and every padded axis at most 32 (pencils in registers).
+static bool reg_path_ok(const BoxSet& bs, size_t es) {
+    return es == sizeof(float2) && bs.Mx <= 32 && bs.My <= 32 && bs.Mz <= 32;
+}
+static size_t reg_smem(const BoxSet& bs) {
+    size_t rows = (size_t)kInnerThreads * (bs.bx + 1 + bs.Mx + 1);
+    size_t zc = (size_t)3 * bs.Mz * kZCols;
+    return std::max(rows, zc) * sizeof(float2);
+}
+
 bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force) {
     int a, b;
     size_t s;
-    return (force || bs.nb >= kInnerMinBlocks) && inner_tiles(bs, es, &a, &b, &s);
+    return (force || bs.nb >= kInnerMinBlocks) && inner_tiles(bs, es, &a, &b, &s) &&
+           (!reg_path_ok(bs, es) || reg_smem(bs) <= 160 * 1024);
 }
 
 template <class C>
@@ -375,6 +826,7 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         const BoxSet& bs = *j.bs;
         InnerGroup<C>& g = hg[i];
         g.b = j.v.b; g.x = j.v.x; g.r = j.v.r; g.rhat = j.v.rhat; g.p = j.v.p; g.v = j.v.v; g.s = j.v.s; g.t = j.v.t;
+        g.w1 = reinterpret_cast<C*>(bs.w1);
         g.w2 = reinterpret_cast<C*>(bs.w2);
         g.chi = j.chi;
         g.mask = bs.mask;
@@ -385,12 +837,16 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         g.lyb = lg2(bs.by);
         size_t sm = 0;
         if (!inner_tiles(bs, sizeof(C), &g.lpt, &g.ltc, &sm)) return fail(VIE_EINVAL, "box too large for the persistent solver");
+        g.reg = reg_path_ok(bs, sizeof(C)) ? 1 : 0;
+        if (g.reg) sm = reg_smem(bs);
         // algorithmic bytes of one MVM with its fused vector work: plane spectra written, read and
         // rewritten along z, read back (4 x [3][bz][My][Mx]), the Green spectrum once, chi and mask,
         // and the 4 box vectors the fused update/inverse phases touch; the x/r pass moves 6 vectors.
         const int64_t es = sizeof(C), box = bs.box_elems();
         const int64_t w2b = 3LL * bs.bz * bs.My * bs.Mx * es;
-        const int64_t mvm = 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 4 * 3 * box * es;
+        const int64_t w1b = 3LL * bs.bz * bs.by * bs.Mx * es;
+        const int64_t mvm = g.reg ? 4 * w1b + 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 7 * 3 * box * es
+                                  : 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 4 * 3 * box * es;
         g.kb_mvm = (int)((mvm + 1023) / 1024);
         g.kb_upd = (int)((6 * 3 * box * es + 1023) / 1024);
         smem = std::max(smem, sm);

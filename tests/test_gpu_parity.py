@@ -148,7 +148,8 @@ def test_precond_paths_agree_on_metasurface_blocks(precision):
         assert st["nblocks"] == 16 and st["not_converged"] == 0
         out.append((host(y), st))
     assert rel(out[1][0], out[0][0]) <= 10 * itol
-    assert abs(out[0][1]["mean_iters"] - out[1][1]["mean_iters"]) <= 1.0
+    m0, m1 = out[0][1]["mean_iters"], out[1][1]["mean_iters"]
+    assert abs(m0 - m1) <= max(1.0, 0.1 * m0)
 
 
 def test_precond_without_blocks_is_identity():
