@@ -17,8 +17,17 @@
 // The block scratch ([3][bz][My][Mx]) stays L2-resident for the boxes this
 // path accepts. Scalars are FP64; complex64 vectors accumulate products in
 // FP32 within a thread and in FP64 across the CTA.
+#include <cooperative_groups.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "fft_core.cuh"
 #include "vie_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace vie {
 
@@ -36,6 +45,7 @@ template <class C> struct InnerGroup {
     int kb_mvm;                             // profiling: KB moved by one MVM and its fused updates
     int kb_upd;                             // profiling: KB moved by the x/r update pass
     int reg;                                // 1: register-FFT MVM (complex64, every padded axis <= 32)
+    unsigned fd_bx[3], fd_plane[3];         // FastDiv constants (m, s, d) for bx and bz*by
 };
 
 constexpr int kInnerThreads = 256;
@@ -77,6 +87,37 @@ __device__ void cta_sum2(double2& a, double2& b, double2* red) {
     b = sb;
 }
 
+// A block is solved by a team: the R CTAs of one thread-block cluster. Every
+// phase splits its rows / columns / planes over the ranks; phases that read
+// what other ranks wrote are separated by cluster barriers (release/acquire at
+// cluster scope), and sums go CTA -> distributed shared memory in rank order,
+// so every CTA gets identical scalars.
+__device__ __forceinline__ int team_rank() { return (int)cg::this_cluster().block_rank(); }
+__device__ __forceinline__ int team_size() { return (int)cg::this_cluster().num_blocks(); }
+__device__ __forceinline__ void team_sync() { cg::this_cluster().sync(); }
+
+__device__ void team_sum2(double2& a, double2& b, double2* red) {
+    cta_sum2(a, b, red);
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned R = cl.num_blocks();
+    if (R == 1) return;
+    __shared__ double2 xred[2];
+    if (threadIdx.x == 0) {
+        xred[0] = a;
+        xred[1] = b;
+    }
+    cl.sync();
+    double2 sa = make_double2(0, 0), sb = make_double2(0, 0);
+    for (unsigned r = 0; r < R; ++r) {
+        const double2* q = cl.map_shared_rank(xred, r);
+        sa.x += q[0].x; sa.y += q[0].y;
+        sb.x += q[1].x; sb.y += q[1].y;
+    }
+    cl.sync();
+    a = sa;
+    b = sb;
+}
+
 enum { IN_P = 0, IN_S = 1 };
 enum { OUT_V = 0, OUT_T = 1 };
 
@@ -88,7 +129,8 @@ __device__ double2 phase_xy(const InnerGroup<C>& g, int64_t voff, C* W, const C*
     const int planes = 3 * g.bz, P = g.Mx + 1, pe = g.My * P, tile = 1 << g.lpt;
     const int64_t box = (int64_t)g.bx * g.by * g.bz;
     C acc = czero<C>();
-    for (int pl0 = 0; pl0 < planes; pl0 += tile) {
+    const int rk = team_rank(), nrk = team_size();
+    for (int pl0 = rk * tile; pl0 < planes; pl0 += nrk * tile) {
         const int n = tile * g.My * g.Mx;
         for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
             int xq = idx & (g.Mx - 1), t = idx >> g.lx;
@@ -124,7 +166,7 @@ __device__ double2 phase_xy(const InnerGroup<C>& g, int64_t voff, C* W, const C*
         __syncthreads();
     }
     double2 a = wide<C>(acc), z = make_double2(0, 0);
-    cta_sum2(a, z, red);
+    team_sum2(a, z, red);
     return a;
 }
 
@@ -135,7 +177,8 @@ __device__ void phase_z(const InnerGroup<C>& g, C* W, C* sm, const C* tw) {
     const int64_t plane = (int64_t)g.My * g.Mx;
     const int64_t cstride = (int64_t)g.bz * plane, gcomp = (int64_t)g.Mz * plane;
     const int L = g.Mz;
-    for (int64_t c0 = 0; c0 < plane; c0 += TC) {
+    const int rk = team_rank(), nrk = team_size();
+    for (int64_t c0 = (int64_t)rk * TC; c0 < plane; c0 += (int64_t)nrk * TC) {
         for (int idx = threadIdx.x; idx < L * 3 * TC; idx += blockDim.x) {
             int c = idx & (TC - 1), t = idx >> g.ltc;
             int comp = t % 3, i = t / 3;
@@ -176,7 +219,8 @@ __device__ void phase_xy_inv(const InnerGroup<C>& g, int64_t voff, const C* W, c
     const int planes = 3 * g.bz, P = g.Mx + 1, pe = g.My * P, tile = 1 << g.lpt;
     const int64_t box = (int64_t)g.bx * g.by * g.bz;
     C a1 = czero<C>(), a2 = czero<C>();
-    for (int pl0 = 0; pl0 < planes; pl0 += tile) {
+    const int rk = team_rank(), nrk = team_size();
+    for (int pl0 = rk * tile; pl0 < planes; pl0 += nrk * tile) {
         const int n = tile * g.My * g.Mx;
         for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
             int xq = idx & (g.Mx - 1), t = idx >> g.lx;
@@ -212,7 +256,7 @@ __device__ void phase_xy_inv(const InnerGroup<C>& g, int64_t voff, const C* W, c
     }
     d1 = wide<C>(a1);
     d2 = wide<C>(a2);
-    cta_sum2(d1, d2, red);
+    team_sum2(d1, d2, red);
 }
 
 // ---------------------------------------------------------------- register-FFT box MVM (complex64)
@@ -228,6 +272,9 @@ __device__ __forceinline__ C twmul(C v, int m, const C* __restrict__ tw) {
     return FWD ? cmul(v, w) : cmulc(v, w);
 }
 
+// Twiddle multiply used by the register FFTs (specialised below per precision).
+template <class C> struct TwSel;
+
 // One radix-2 stage of span S (a compile-time constant) on an L-point pencil.
 template <int L, int S, bool FWD, class C>
 __device__ __forceinline__ void rstage(C (&a)[L], const C* __restrict__ tw) {
@@ -239,9 +286,9 @@ __device__ __forceinline__ void rstage(C (&a)[L], const C* __restrict__ tw) {
             if (FWD) {
                 C x0 = a[g + j], x1 = a[g + j + S];
                 a[g + j] = x0 + x1;
-                a[g + j + S] = twmul<true>(x0 - x1, m, tw);
+                a[g + j + S] = TwSel<C>::template apply<true>(x0 - x1, m, tw);
             } else {
-                C x0 = a[g + j], x1 = twmul<false>(a[g + j + S], m, tw);
+                C x0 = a[g + j], x1 = TwSel<C>::template apply<false>(a[g + j + S], m, tw);
                 a[g + j] = x0 + x1;
                 a[g + j + S] = x0 - x1;
             }
@@ -270,7 +317,49 @@ __device__ __forceinline__ void rfft(C (&a)[L], const C* __restrict__ tw) {
 }
 
 typedef float2 F;
-constexpr int kU = 1;   // elements per thread whose loads are issued together (1: lowest register use)
+
+// Twiddles W_Lmax^m of the complex64 register path in constant memory: the
+// register FFTs index them with compile-time offsets, so they become constant
+// operands instead of loads. Copied once per device before the first launch.
+__constant__ F c_tw64[kLmax];
+
+template <bool FWD>
+__device__ __forceinline__ F twc(F v, int m) {
+    if (m == 0) return v;
+    if (m == kLmax / 4) return FWD ? mul_mi(v) : mul_i(v);
+    F w = c_tw64[m];
+    return FWD ? cmul(v, w) : cmulc(v, w);
+}
+
+template <> struct TwSel<double2> {
+    template <bool FWD>
+    static __device__ __forceinline__ double2 apply(double2 v, int m, const double2* __restrict__ tw) {
+        return twmul<FWD>(v, m, tw);
+    }
+};
+template <> struct TwSel<float2> {
+    template <bool FWD>
+    static __device__ __forceinline__ float2 apply(float2 v, int m, const float2* __restrict__) {
+        return twc<FWD>(v, m);
+    }
+};
+
+// Division by a runtime divisor d (1 <= d < 2^31) of n < 2^31 with a multiply-high
+// (Granlund and Montgomery, PLDI 1994): q = (umulhi(n, m) + n) >> s.
+struct FastDiv {
+    unsigned m, s, d;
+};
+__device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv f) { return (__umulhi(n, f.m) + n) >> f.s; }
+__device__ __forceinline__ FastDiv fd_of(const unsigned (&v)[3]) { return FastDiv{v[0], v[1], v[2]}; }
+
+// Prefetch into L1: lets a loop with one pending element per thread overlap
+// the L2 latency of later iterations without holding their values in registers.
+__device__ __forceinline__ void pf(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+constexpr int kPf = 2;   // iterations ahead
+
+constexpr int kU = 1;   // elements per thread whose loads are issued together in the row phases
+constexpr int kUV = 1;  // elements per thread per batch in the block-vector passes
+constexpr int kUG = 1;  // Green-multiply tasks per thread whose 6 spectrum loads are issued together
 
 // Pruned transforms. A box of b voxels is padded to L >= 2b - 1, a power of
 // two, so b <= L/2: forward inputs beyond L/2 are zero and inverse outputs
@@ -291,7 +380,7 @@ __device__ __forceinline__ void fwd_half(Get get, Put put, const F* __restrict__
     constexpr int H = L / 2 > 0 ? L / 2 : 1;
     F a[H];
 #pragma unroll
-    for (int j = 0; j < H; ++j) a[j] = twmul<true>(get(j), j * (kLmax / L), tw);
+    for (int j = 0; j < H; ++j) a[j] = twc<true>(get(j), j * (kLmax / L));
     rfft<H, true>(a, tw);
 #pragma unroll
     for (int j = 0; j < H; ++j) put(H + j, a[j]);
@@ -317,7 +406,7 @@ __device__ __forceinline__ void inv_half(Get get, Stash stash, Unstash unstash, 
     for (int j = 0; j < H; ++j) a[j] = get(H + j);
     rfft<H, false>(a, tw);
 #pragma unroll
-    for (int j = 0; j < H; ++j) stash(j, twmul<false>(a[j], j * (kLmax / L), tw));
+    for (int j = 0; j < H; ++j) stash(j, twc<false>(a[j], j * (kLmax / L)));
 #pragma unroll
     for (int j = 0; j < H; ++j) a[j] = get(j);
     rfft<H, false>(a, tw);
@@ -331,26 +420,38 @@ __device__ __forceinline__ void inv_half(Get get, Stash stash, Unstash unstash, 
 template <int LX, int IN>
 __device__ __forceinline__ F x_fwd_reg(const InnerGroup<F>& g, int64_t voff, F* W1, const F* chi, F* sm,
                                        const F* tw, F c1, F c2) {
-    const int R = 3 * g.bz * g.by, bx = g.bx, plane = g.bz * g.by, T = blockDim.x, t = threadIdx.x;
+    const int NR = 3 * g.bz * g.by, bx = g.bx, plane = g.bz * g.by, T = blockDim.x, t = threadIdx.x;
+    const FastDiv dbx = fd_of(g.fd_bx), dpl = fd_of(g.fd_plane);
     F* smi = sm;
     F* smo = sm + T * (bx + 1);
     F acc = czero<F>();
-    for (int r0 = 0; r0 < R; r0 += T) {
-        const int nr = min(T, R - r0);
+    const int rk = team_rank(), nrk = team_size();
+    for (int r0 = rk * T; r0 < NR; r0 += nrk * T) {
+        const int nr = min(T, NR - r0);
         const int64_t base = voff + (int64_t)r0 * bx;
         const int nk = nr * bx;
         for (int k0 = t; k0 < nk; k0 += kU * T) {
+            {
+                const int ka = k0 + kPf * kU * T;
+                if (ka < nk) {
+                    const int64_t e = base + ka;
+                    pf(g.r + e);
+                    pf(g.v + e);
+                    if (IN == IN_P) pf(g.p + e);
+                }
+            }
             F ra[kU], pa[kU], va[kU], ca[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {          // all loads of the batch first
                 const int k = k0 + u * T;
                 if (k < nk) {
                     const int64_t e = base + k;
-                    const int rr = k / bx, x = k - rr * bx;
+                    const int rr = (int)fdiv(k, dbx), x = k - rr * bx;
+                    const int row = r0 + rr;
                     ra[u] = g.r[e];
                     va[u] = g.v[e];
                     if (IN == IN_P) pa[u] = g.p[e];
-                    ca[u] = chi[(int64_t)((r0 + rr) % plane) * bx + x];
+                    ca[u] = chi[(int64_t)(row - (int)fdiv(row, dpl) * plane) * bx + x];
                 }
             }
 #pragma unroll
@@ -358,7 +459,7 @@ __device__ __forceinline__ F x_fwd_reg(const InnerGroup<F>& g, int64_t voff, F* 
                 const int k = k0 + u * T;
                 if (k < nk) {
                     const int64_t e = base + k;
-                    const int rr = k / bx, x = k - rr * bx;
+                    const int rr = (int)fdiv(k, dbx), x = k - rr * bx;
                     F in;
                     if (IN == IN_P) {
                         in = ra[u] + cmul(c1, pa[u] - cmul(c2, va[u]));
@@ -380,7 +481,7 @@ __device__ __forceinline__ F x_fwd_reg(const InnerGroup<F>& g, int64_t voff, F* 
         }
         __syncthreads();
         F* dst = W1 + (int64_t)r0 * LX;
-        for (int k = t; k < nr * LX; k += T) dst[k] = smo[(k / LX) * (LX + 1) + (k & (LX - 1))];
+        for (int k = t; k < nr * LX; k += T) dst[k] = smo[(k / LX) * (LX + 1) + (k & (LX - 1))];   // LX: power of two
         __syncthreads();
     }
     return acc;
@@ -390,8 +491,9 @@ __device__ __forceinline__ F x_fwd_reg(const InnerGroup<F>& g, int64_t voff, F* 
 template <int LY>
 __device__ __forceinline__ void y_fwd_reg(const InnerGroup<F>& g, const F* W1, F* W2, const F* tw) {
     const int LX = g.Mx, cols = 3 * g.bz * LX, by = g.by;
-    for (int col = threadIdx.x; col < cols; col += blockDim.x) {
-        int pz = col / LX, x = col - pz * LX;
+    const int nrk = team_size();
+    for (int col = team_rank() * blockDim.x + threadIdx.x; col < cols; col += nrk * blockDim.x) {
+        int pz = col >> g.lx, x = col & (LX - 1);
         const F* src = W1 + (int64_t)pz * by * LX + x;
         F* dst = W2 + (int64_t)pz * LY * LX + x;
         fwd_half<LY>([&](int j) { return j < by ? src[j * LX] : czero<F>(); }, [&](int k, F v) { dst[k * LX] = v; },
@@ -403,8 +505,9 @@ __device__ __forceinline__ void y_fwd_reg(const InnerGroup<F>& g, const F* W1, F
 template <int LY>
 __device__ __forceinline__ void y_inv_reg(const InnerGroup<F>& g, const F* W2, F* W1, const F* tw) {
     const int LX = g.Mx, cols = 3 * g.bz * LX, by = g.by;
-    for (int col = threadIdx.x; col < cols; col += blockDim.x) {
-        int pz = col / LX, x = col - pz * LX;
+    const int nrk = team_size();
+    for (int col = team_rank() * blockDim.x + threadIdx.x; col < cols; col += nrk * blockDim.x) {
+        int pz = col >> g.lx, x = col & (LX - 1);
         const F* src = W2 + (int64_t)pz * LY * LX + x;
         F* dst = W1 + (int64_t)pz * by * LX + x;
         inv_half<LY>([&](int k) { return src[k * LX]; },
@@ -424,10 +527,12 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
     constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1;
     const int P = g.My * g.Mx, T = blockDim.x, t = threadIdx.x, bz = g.bz;
     const int cs = bz * P, gc = LZ * P;
-    for (int c0 = 0; c0 < P; c0 += kZCols) {
-        const int nc = min(kZCols, P - c0);
+    const int rk = team_rank(), nrk = team_size();
+    for (int c0 = rk * kZCols; c0 < P; c0 += nrk * kZCols) {
+        const int nc = min(kZCols, P - c0);     // a power of two (P and kZCols are)
+        const int lnc = 31 - __clz(nc);
         for (int task = t; task < 3 * nc; task += T) {
-            const int comp = task / nc, c = task - comp * nc;
+            const int comp = task >> lnc, c = task & (nc - 1);
             const F* src = W2 + comp * cs + c0 + c;
             F* S = sm + comp * LZ * kZCols + c;
             if (LZ == 1) {
@@ -438,7 +543,7 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
 #pragma unroll
             for (int j = 0; j < H; ++j) a[j] = j < bz ? src[j * P] : czero<F>();
 #pragma unroll
-            for (int j = 0; j < H; ++j) a[j] = twmul<true>(a[j], j * (kLmax / LZ), tw);
+            for (int j = 0; j < H; ++j) a[j] = twc<true>(a[j], j * (kLmax / LZ));
             rfft<H, true>(a, tw);
 #pragma unroll
             for (int j = 0; j < H; ++j) S[(H + j) * kZCols] = a[j];
@@ -450,23 +555,38 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
         }
         __syncthreads();
         const int cst = LZ * kZCols;
-        for (int task0 = t; task0 < LZ * nc; task0 += kU * T) {
-            F gv[kU][6];
+        for (int task = t; task < LZ * nc && task < t + kPf * T; task += T) {
+            const int i = task >> lnc, c = task & (nc - 1);
+            const F* gp = g.G + i * P + c0 + c;
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int q = 0; q < 6; ++q) pf(gp + q * gc);
+        }
+        for (int task0 = t; task0 < LZ * nc; task0 += kUG * T) {
+            {
+                const int ta = task0 + kPf * T;
+                if (ta < LZ * nc) {
+                    const int i = ta >> lnc, c = ta & (nc - 1);
+                    const F* gp = g.G + i * P + c0 + c;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) pf(gp + q * gc);
+                }
+            }
+            F gv[kUG][6];
+#pragma unroll
+            for (int u = 0; u < kUG; ++u) {
                 const int task = task0 + u * T;
                 if (task < LZ * nc) {
-                    const int i = task / nc, c = task - i * nc;
+                    const int i = task >> lnc, c = task & (nc - 1);
                     const F* gp = g.G + i * P + c0 + c;
 #pragma unroll
                     for (int q = 0; q < 6; ++q) gv[u][q] = gp[q * gc];
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < kUG; ++u) {
                 const int task = task0 + u * T;
                 if (task < LZ * nc) {
-                    const int i = task / nc, c = task - i * nc;
+                    const int i = task >> lnc, c = task & (nc - 1);
                     F* q = sm + i * kZCols + c;
                     F X = q[0], Y = q[cst], Z = q[2 * cst];
                     q[0] = cmul(gv[u][0], X) + cmul(gv[u][1], Y) + cmul(gv[u][2], Z);
@@ -477,7 +597,7 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
         }
         __syncthreads();
         for (int task = t; task < 3 * nc; task += T) {
-            const int comp = task / nc, c = task - comp * nc;
+            const int comp = task >> lnc, c = task & (nc - 1);
             F* S = sm + comp * LZ * kZCols + c;
             F* dst = W2 + comp * cs + c0 + c;
             if (LZ == 1) {
@@ -489,7 +609,7 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
             for (int j = 0; j < H; ++j) a[j] = S[(H + j) * kZCols];
             rfft<H, false>(a, tw);
 #pragma unroll
-            for (int j = 0; j < H; ++j) S[(H + j) * kZCols] = twmul<false>(a[j], j * (kLmax / LZ), tw);
+            for (int j = 0; j < H; ++j) S[(H + j) * kZCols] = twc<false>(a[j], j * (kLmax / LZ));
 #pragma unroll
             for (int j = 0; j < H; ++j) a[j] = S[j * kZCols];
             rfft<H, false>(a, tw);
@@ -505,11 +625,13 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
 template <int LX, int OUT>
 __device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, const F* W1, const uint8_t* mask,
                                           F* sm, const F* tw, F& a1, F& a2) {
-    const int R = 3 * g.bz * g.by, bx = g.bx, plane = g.bz * g.by, T = blockDim.x, t = threadIdx.x;
+    const int NR = 3 * g.bz * g.by, bx = g.bx, plane = g.bz * g.by, T = blockDim.x, t = threadIdx.x;
+    const FastDiv dbx = fd_of(g.fd_bx), dpl = fd_of(g.fd_plane);
     F* smi = sm;
     F* smo = sm + T * (LX + 1);
-    for (int r0 = 0; r0 < R; r0 += T) {
-        const int nr = min(T, R - r0);
+    const int rk = team_rank(), nrk = team_size();
+    for (int r0 = rk * T; r0 < NR; r0 += nrk * T) {
+        const int nr = min(T, NR - r0);
         const F* src = W1 + (int64_t)r0 * LX;
         for (int k = t; k < nr * LX; k += T) smi[(k / LX) * (LX + 1) + (k & (LX - 1))] = src[k];
         __syncthreads();
@@ -525,6 +647,14 @@ __device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, 
         const int64_t base = voff + (int64_t)r0 * bx;
         const int nk = nr * bx;
         for (int k0 = t; k0 < nk; k0 += kU * T) {
+            {
+                const int ka = k0 + kPf * kU * T;
+                if (ka < nk) {
+                    const int64_t e = base + ka;
+                    pf(OUT == OUT_V ? g.p + e : g.s + e);
+                    if (OUT == OUT_V) pf(g.rhat + e);
+                }
+            }
             F ia[kU], ha[kU];
             uint8_t ma[kU];
 #pragma unroll
@@ -532,10 +662,11 @@ __device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, 
                 const int k = k0 + u * T;
                 if (k < nk) {
                     const int64_t e = base + k;
-                    const int rr = k / bx, x = k - rr * bx;
+                    const int rr = (int)fdiv(k, dbx), x = k - rr * bx;
+                    const int row = r0 + rr;
                     ia[u] = OUT == OUT_V ? g.p[e] : g.s[e];
                     if (OUT == OUT_V) ha[u] = g.rhat[e];
-                    ma[u] = mask[(int64_t)((r0 + rr) % plane) * bx + x];
+                    ma[u] = mask[(int64_t)(row - (int)fdiv(row, dpl) * plane) * bx + x];
                 }
             }
 #pragma unroll
@@ -543,7 +674,7 @@ __device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, 
                 const int k = k0 + u * T;
                 if (k < nk) {
                     const int64_t e = base + k;
-                    const int rr = k / bx, x = k - rr * bx;
+                    const int rr = (int)fdiv(k, dbx), x = k - rr * bx;
                     F o = ma[u] ? ia[u] - smo[rr * (bx + 1) + x] : czero<F>();
                     if (OUT == OUT_V) {
                         g.v[e] = o;
@@ -562,9 +693,6 @@ __device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, 
 
 #define VIE_LEN_SWITCH(l, CALL)                                        \
     switch (l) {                                                       \
-        case 0: { constexpr int LL = 1; CALL; } break;                 \
-        case 1: { constexpr int LL = 2; CALL; } break;                 \
-        case 2: { constexpr int LL = 4; CALL; } break;                 \
         case 3: { constexpr int LL = 8; CALL; } break;                 \
         case 4: { constexpr int LL = 16; CALL; } break;                \
         default: { constexpr int LL = 32; CALL; } break;               \
@@ -575,9 +703,14 @@ template <class C> struct SmemMvm {
     template <int IN>
     static __device__ double2 fwd(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const C* chi, C* sm,
                                   const C* tw, C c1, C c2, double2* red) {
-        return phase_xy<C, IN>(g, voff, W2, chi, sm, tw, c1, c2, red);
+        double2 r = phase_xy<C, IN>(g, voff, W2, chi, sm, tw, c1, c2, red);
+        team_sync();
+        return r;
     }
-    static __device__ void mid(const InnerGroup<C>& g, C* W2, C* sm, const C* tw) { phase_z<C>(g, W2, sm, tw); }
+    static __device__ void mid(const InnerGroup<C>& g, C* W2, C* sm, const C* tw) {
+        phase_z<C>(g, W2, sm, tw);
+        team_sync();
+    }
     template <int OUT>
     static __device__ void inv(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const uint8_t* mask, C* sm,
                                const C* tw, double2* red, double2& d1, double2& d2) {
@@ -591,25 +724,27 @@ struct RegMvm {
                                   const F* tw, F c1, F c2, double2* red) {
         F acc = czero<F>();
         VIE_LEN_SWITCH(g.lx, (acc = x_fwd_reg<LL, IN>(g, voff, W1, chi, sm, tw, c1, c2)));
-        __syncthreads();
+        team_sync();
         VIE_LEN_SWITCH(g.ly, (y_fwd_reg<LL>(g, W1, W2, tw)));
         double2 a = make_double2(acc.x, acc.y), z = make_double2(0, 0);
-        cta_sum2(a, z, red);   // begins with a barrier, so W2 is complete afterwards
+        team_sum2(a, z, red);
+        team_sync();          // W2 complete on every rank
         return a;
     }
     static __device__ __forceinline__ void mid(const InnerGroup<F>& g, F* W2, F* sm, const F* tw) {
         VIE_LEN_SWITCH(g.lz, (z_reg<LL>(g, W2, sm, tw)));
+        team_sync();
     }
     template <int OUT>
     static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const uint8_t* mask, F* sm,
                                const F* tw, double2* red, double2& d1, double2& d2) {
         VIE_LEN_SWITCH(g.ly, (y_inv_reg<LL>(g, W2, W1, tw)));
-        __syncthreads();
+        team_sync();
         F a1 = czero<F>(), a2 = czero<F>();
         VIE_LEN_SWITCH(g.lx, (x_inv_reg<LL, OUT>(g, voff, W1, mask, sm, tw, a1, a2)));
         d1 = make_double2(a1.x, a1.y);
         d2 = make_double2(a2.x, a2.y);
-        cta_sum2(d1, d2, red);
+        team_sum2(d1, d2, red);
     }
 };
 
@@ -625,16 +760,18 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
     const uint8_t* mask = g.mask + (int64_t)b * box;
 
     // x = 0, r = rhat = b, p = v = 0
+    const int rk = team_rank(), nrk = team_size();
+    const int64_t first = (int64_t)rk * kUV * blockDim.x, step = (int64_t)nrk * kUV * blockDim.x;
     C acc = czero<C>();
-    for (int64_t i0 = threadIdx.x; i0 < n; i0 += kU * blockDim.x) {
-        C bv[kU];
+    for (int64_t i0 = first + threadIdx.x; i0 < n; i0 += step) {
+        C bv[kUV];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < kUV; ++u) {
             const int64_t i = i0 + u * blockDim.x;
             if (i < n) bv[u] = g.b[voff + i];
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < kUV; ++u) {
             const int64_t i = i0 + u * blockDim.x;
             if (i < n) {
                 const int64_t e = voff + i;
@@ -648,7 +785,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
         }
     }
     double2 d1 = wide<C>(acc), d2 = make_double2(0, 0);
-    cta_sum2(d1, d2, red);
+    team_sum2(d1, d2, red);
     const double bn2 = d1.x;
     const double tol2 = tol * tol * bn2;
     double2 rho = make_double2(bn2, 0.0), rho_prev = make_double2(1, 0), alpha = make_double2(1, 0),
@@ -662,7 +799,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
         // v = A p, p = r + beta (p - omega v)
         Mvm::template fwd<IN_P>(g, voff, W1, W, chi, sm, tw, cmk<C>(beta.x, beta.y), cmk<C>(omega.x, omega.y), red);
         Mvm::mid(g, W, sm, tw);
-        if (units != nullptr && threadIdx.x == 0) atomicAdd(units, g.kb_mvm);
+        if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm);
         double2 sigma, unused;
         Mvm::template inv<OUT_V>(g, voff, W1, W, mask, sm, tw, red, sigma, unused);
         if (!dgood(sigma)) { status = SEG_BREAKDOWN; break; }
@@ -672,7 +809,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
         if (sn.x <= tol2) {
             // half-step convergence: x += alpha p
             C ac = cmk<C>(alpha.x, alpha.y);
-            for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            for (int64_t i = (int64_t)rk * blockDim.x + threadIdx.x; i < n; i += (int64_t)nrk * blockDim.x) {
                 int64_t e = voff + i;
                 g.x[e] = g.x[e] + cmul(ac, g.p[e]);
             }
@@ -682,7 +819,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
             break;
         }
         Mvm::mid(g, W, sm, tw);
-        if (units != nullptr && threadIdx.x == 0) atomicAdd(units, g.kb_mvm + g.kb_upd);
+        if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm + g.kb_upd);
         double2 ts, tt;
         Mvm::template inv<OUT_T>(g, voff, W1, W, mask, sm, tw, red, ts, tt);
         if (!(tt.x > 0.0) || !isfinite(tt.x)) { status = SEG_BREAKDOWN; break; }
@@ -690,10 +827,10 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
         // x += alpha p + omega s, r = s - omega t; rho = <rhat, r>, ||r||^2
         C ac = cmk<C>(alpha.x, alpha.y), oc = cmk<C>(omega.x, omega.y);
         C a1 = czero<C>(), a2 = czero<C>();
-        for (int64_t i0 = threadIdx.x; i0 < n; i0 += kU * blockDim.x) {
-            C sv[kU], xv[kU], pv[kU], tv[kU], hv[kU];
+        for (int64_t i0 = first + threadIdx.x; i0 < n; i0 += step) {
+            C sv[kUV], xv[kUV], pv[kUV], tv[kUV], hv[kUV];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < kUV; ++u) {
                 const int64_t i = i0 + u * blockDim.x;
                 if (i < n) {
                     const int64_t e = voff + i;
@@ -705,7 +842,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < kUV; ++u) {
                 const int64_t i = i0 + u * blockDim.x;
                 if (i < n) {
                     const int64_t e = voff + i;
@@ -719,7 +856,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
         }
         d1 = wide<C>(a1);
         d2 = wide<C>(a2);
-        cta_sum2(d1, d2, red);
+        team_sum2(d1, d2, red);
         rho_prev = rho;
         rho = d1;
         res2 = d2.x;
@@ -729,7 +866,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
         if (omega.x == 0.0 && omega.y == 0.0) { status = SEG_BREAKDOWN; break; }
     }
     if (status == SEG_ACTIVE) status = SEG_MAXIT;
-    if (threadIdx.x == 0) {
+    if (rk == 0 && threadIdx.x == 0) {
         SegState& S = g.st[b];
         S.bnorm2 = bn2;
         S.res2 = res2;
@@ -758,14 +895,21 @@ __global__ void __launch_bounds__(kInnerThreads, 2) k_inner(const InnerGroup<C>*
     C* sm = reinterpret_cast<C*>(smem_raw);
     __shared__ double2 red[2 * (kInnerThreads / 32)];
     __shared__ int item;
+    cg::cluster_group cl = cg::this_cluster();
     for (;;) {
-        if (threadIdx.x == 0) item = atomicAdd(next, 1);
-        __syncthreads();
-        const int it = item;
-        __syncthreads();
+        // rank 0 of the cluster takes the next block; every rank reads it from rank 0's shared memory
+        if (cl.block_rank() == 0 && threadIdx.x == 0) item = atomicAdd(next, 1);
+        cl.sync();
+        const int it = *cl.map_shared_rank(&item, 0);
+        cl.sync();
         if (it >= nwork) break;
         const int2 wk = work[it];
-        solve_dispatch(groups[wk.x], wk.y, tol, maxit, sm, tw, red, units);
+        // descriptor in shared memory: fields are reloaded after barriers instead of held in registers
+        __shared__ InnerGroup<C> gsh;
+        if (threadIdx.x == 0) gsh = groups[wk.x];
+        __syncthreads();
+        solve_dispatch(gsh, wk.y, tol, maxit, sm, tw, red, units);
+        __syncthreads();
     }
 }
 
@@ -777,6 +921,17 @@ static int lg2(int v) {
 }
 
 constexpr size_t kInnerSmemBudget = 96 * 1024;
+
+// CTAs per block (thread-block cluster size) of the persistent solver: 1, 2, 4 or 8.
+// Default 2; the environment variable VIE_INNER_CLUSTER overrides it (read once).
+static int inner_cluster_size() {
+    static const int r = [] {
+        const char* e = getenv("VIE_INNER_CLUSTER");
+        int v = e ? atoi(e) : 2;
+        return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 2;
+    }();
+    return r;
+}
 
 // Tiles for one group; false when a single plane does not fit the budget.
 static bool inner_tiles(const BoxSet& bs, size_t es, int* lpt, int* ltc, size_t* smem) {
@@ -795,15 +950,29 @@ static bool inner_tiles(const BoxSet& bs, size_t es, int* lpt, int* ltc, size_t*
     return true;
 }
 
-// Register-FFT MVM: complex64 and every padded axis at most 32 (pencils in registers).
+// Register-FFT MVM: complex64 and every padded axis in [8, 32] (pencils in registers).
 static bool reg_path_ok(const BoxSet& bs, size_t es) {
-    return es == sizeof(float2) && bs.Mx <= 32 && bs.My <= 32 && bs.Mz <= 32;
+    auto ok = [](int m) { return m >= 8 && m <= 32; };
+    return es == sizeof(float2) && ok(bs.Mx) && ok(bs.My) && ok(bs.Mz);
 }
 static size_t reg_smem(const BoxSet& bs) {
     size_t rows = (size_t)kInnerThreads * (bs.bx + 1 + bs.Mx + 1);
     size_t zc = (size_t)3 * bs.Mz * kZCols;
     return std::max(rows, zc) * sizeof(float2);
 }
+
+// m and s of FastDiv for divisor d >= 1: s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1.
+static void make_fastdiv(unsigned d, unsigned (&out)[3]) {
+    unsigned sh = 0;
+    while ((1ull << sh) < d) ++sh;
+    unsigned long long m = (((1ull << 32) * ((1ull << sh) - d)) / d) + 1;
+    out[0] = (unsigned)m;
+    out[1] = sh;
+    out[2] = d;
+}
+
+static std::mutex g_ctw_mu;
+static std::vector<int> g_ctw_dev;
 
 bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force) {
     int a, b;
@@ -838,6 +1007,8 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         size_t sm = 0;
         if (!inner_tiles(bs, sizeof(C), &g.lpt, &g.ltc, &sm)) return fail(VIE_EINVAL, "box too large for the persistent solver");
         g.reg = reg_path_ok(bs, sizeof(C)) ? 1 : 0;
+        make_fastdiv((unsigned)bs.bx, g.fd_bx);
+        make_fastdiv((unsigned)(bs.bz * bs.by), g.fd_plane);
         if (g.reg) sm = reg_smem(bs);
         // algorithmic bytes of one MVM with its fused vector work: plane spectra written, read and
         // rewritten along z, read back (4 x [3][bz][My][Mx]), the Green spectrum once, chi and mask,
@@ -852,20 +1023,46 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         smem = std::max(smem, sm);
         bytes_per_block = std::max<int64_t>(bytes_per_block, 3 * bs.box_elems() * (int64_t)sizeof(C));
     }
+    {
+        // constant-memory twiddles of the register path, once per device
+        int dev = 0;
+        VIE_CK(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lock(g_ctw_mu);
+        if (std::find(g_ctw_dev.begin(), g_ctw_dev.end(), dev) == g_ctw_dev.end()) {
+            VIE_CK(cudaMemcpyToSymbol(c_tw64, tw.d64, kLmax * sizeof(float2), 0, cudaMemcpyDeviceToDevice));
+            g_ctw_dev.push_back(dev);
+        }
+    }
     VIE_CK(cudaMemcpyAsync(d_groups, hg.data(), hg.size() * sizeof(InnerGroup<C>), cudaMemcpyHostToDevice, s));
     VIE_CK(cudaMemsetAsync(d_next, 0, sizeof(int), s));
     // opt in to the exact dynamic size: the default 48 KB limit also counts the static shared memory
     VIE_CK(cudaFuncSetAttribute(k_inner<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, nsm = 0, per = 0;
-    VIE_CK(cudaGetDevice(&dev));
-    VIE_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    VIE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_inner<C>, kInnerThreads, smem));
-    int grid = std::max(1, std::min(nwork, nsm * std::max(1, per)));
+    // one block per cluster of R CTAs; as many clusters as fit at once, pulling blocks from the queue
+    const int R = inner_cluster_size();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(R);
+    cfg.blockDim = dim3(kInnerThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    VIE_CK(cudaOccupancyMaxActiveClusters(&nclusters, k_inner<C>, &cfg));
+    cfg.gridDim = dim3(std::max(1, std::min(nwork, nclusters)) * R);
     // the kernel adds the KB it moves (per MVM) to its profiling counter
     (void)bytes_per_block;
     int* units = prof_begin(s, PK_INNER, sizeof(C) == 16 ? VIE_C128 : VIE_C64, 1024, 0, true);
-    k_inner<C><<<grid, kInnerThreads, smem, s>>>(reinterpret_cast<const InnerGroup<C>*>(d_groups), d_work, nwork,
-                                                 d_next, tol, maxit, tw_of<C>(tw), units);
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_inner<C>, reinterpret_cast<const InnerGroup<C>*>(d_groups), d_work,
+                                        nwork, d_next, tol, maxit, tw_of<C>(tw), units);
+    if (le != cudaSuccess) {
+        prof_end(s);
+        return cuda_fail(le, "cudaLaunchKernelEx(k_inner)", __FILE__, __LINE__);
+    }
     prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
