@@ -219,6 +219,32 @@ int vie_profile_enable(int enable);
  * VIE_ENOMEM (more launches than the profile holds: 1,048,576). */
 int vie_profile_read(vie_kernel_stat* out, int cap, int* n_out, int64_t* total_launches);
 
+/* y = A x (as vie_matvec, complex128) for small grids WITHOUT ANY DEVICE
+ * ALLOCATION. The paper has no counterpart: this entry point exists for
+ * callers that must not allocate device memory at run time, such as code in a
+ * process whose device memory is owned by another framework's allocator, a
+ * real-time loop that cannot block on the driver's allocator, or a deployment
+ * that forbids allocation after start-up. It needs no grid or spectrum
+ * handle: it computes the Green spectrum (FP64) and the MVM with all
+ * intermediates in one static device array of 4,341,760 bytes (about 4.1 MB)
+ * that every device using the library holds until the process exits.
+ *   nx, ny, nz: grid; the padded FFT volume nextpow2(2nx-1) * nextpow2(2ny-1)
+ *       * nextpow2(2nz-1) must be at most 32768 (a 16x16x16 grid fits), else
+ *       VIE_EINVAL with the limit in the message;
+ *   h, k0: voxel edge and wavenumber (> 0);
+ *   chi_dev: DEVICE, complex128 (re, im) chi = eps_r - 1, [nz][ny][nx];
+ *   x_dev, y_dev: DEVICE, complex128 [3][nz][ny][nx], must not overlap.
+ * The first call on a device, with that device current, resolves the array's
+ * device address and writes its twiddle table (a synchronous host-to-device
+ * copy); make that first call before any stream capture. Later calls only
+ * enqueue kernels on `stream`. All calls share the one array and overwrite
+ * it: calls that overlap on the GPU (different streams, or different host
+ * threads without ordering) race and give wrong results. Nothing in the array
+ * needs to start at zero. Errors: VIE_EINVAL, VIE_ECUDA. */
+int vie_matvec_noalloc(int32_t nx, int32_t ny, int32_t nz, double h, double k0,
+                       const double* chi_dev, const double* x_dev, double* y_dev,
+                       vie_stream_t stream);
+
 /* Copies the text of the last error on this thread into buf (NUL-terminated,
  * truncated to len). Returns the length of the full message. */
 int vie_last_error(char* buf, size_t len);

@@ -286,9 +286,11 @@ template <> const double2* chi_ptr<double2>(const BoxSet& bs) { return bs.chi128
 template <> const float2* chi_ptr<float2>(const BoxSet& bs) { return bs.chi64; }
 
 template <class C>
-int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st, cudaStream_t s) {
+int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st, cudaStream_t s,
+              const Twiddles* twp) {
     Twiddles tw;
-    VIE_TRY(get_twiddles(&tw));
+    if (twp) tw = *twp;
+    else VIE_TRY(get_twiddles(&tw));
     const C* T = tw_ptr<C>(tw);
     C* w1 = reinterpret_cast<C*>(bs.w1);
     C* w2 = reinterpret_cast<C*>(bs.w2);
@@ -348,9 +350,10 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
 }
 
 template <class C>
-int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s) {
+int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* twp) {
     Twiddles tw;
-    VIE_TRY(get_twiddles(&tw));
+    if (twp) tw = *twp;
+    else VIE_TRY(get_twiddles(&tw));
     const C* T = tw_ptr<C>(tw);
     const int64_t planeXY = (int64_t)bs.Mx * bs.My;
     const int64_t vol = planeXY * bs.Mz;
@@ -382,8 +385,10 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s) {
     return VIE_OK;
 }
 
-template int mvm_boxes<double2>(const BoxSet&, const double2*, const double2*, double2*, const SegState*, cudaStream_t);
-template int mvm_boxes<float2>(const BoxSet&, const float2*, const float2*, float2*, const SegState*, cudaStream_t);
-template int spectrum_fft<double2>(const BoxSet&, double2*, cudaStream_t);
+template int mvm_boxes<double2>(const BoxSet&, const double2*, const double2*, double2*, const SegState*, cudaStream_t,
+                                const Twiddles*);
+template int mvm_boxes<float2>(const BoxSet&, const float2*, const float2*, float2*, const SegState*, cudaStream_t,
+                               const Twiddles*);
+template int spectrum_fft<double2>(const BoxSet&, double2*, cudaStream_t, const Twiddles*);
 
 }  // namespace vie

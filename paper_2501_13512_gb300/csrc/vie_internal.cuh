@@ -193,11 +193,12 @@ int* prof_begin(cudaStream_t s, int kind, int precision, int64_t bytes_per_unit,
 void prof_end(cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers (fft.cu)
+// tw: twiddle tables to use; null = the per-device tables of get_twiddles()
 template <class C>
 int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st,
-              cudaStream_t s);
+              cudaStream_t s, const Twiddles* tw = nullptr);
 template <class C>
-int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s);   // in place, 6 components
+int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* tw = nullptr);   // in place, 6 components
 
 // ---------------------------------------------------------------- green.cu
 int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t s);

@@ -98,6 +98,7 @@ def load(path=LIB_PATH):
         "vie_matvec": ([P, P, c_int, P, P, P], c_int),
         "vie_block_precond_apply": ([P, P, c_int, P, P, c_double, c_int, P, POINTER(PrecondStats)], c_int),
         "vie_solve": ([P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
+        "vie_matvec_noalloc": ([c_int32, c_int32, c_int32, c_double, c_double, P, P, P, P], c_int),
         "vie_profile_enable": ([c_int], c_int),
         "vie_profile_read": ([POINTER(KernelStat), c_int, POINTER(c_int), POINTER(c_int64)], c_int),
     }
