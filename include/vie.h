@@ -194,6 +194,47 @@ int vie_solve(vie_grid* grid, const vie_spectrum* spectrum, const void* einc_dev
               void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
               vie_solve_stats* stats);
 
+/* ---- Batched independent solves (many instances of one grid shape). ---- */
+typedef struct vie_batch vie_batch;
+
+typedef struct {
+    int32_t nx, ny, nz;      /* grid of every instance, each in [1, 512]               */
+    double h;                /* voxel edge                                             */
+    int32_t count;           /* instances, in [1, 21845]                               */
+    const double* eps_r;     /* HOST, count * 2 * nx*ny*nz doubles: eps_r (re, im) of
+                                instance i at [i][nz][ny][nx]; copied                  */
+    uint32_t flags;          /* reserved, must be 0                                    */
+} vie_batch_desc;
+
+/* Creates `count` independent instances of the unpreconditioned system of Eq. 4
+ * (each its own permittivity) sharing one grid shape, with all workspace.
+ * Errors: VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA. */
+int vie_batch_create(const vie_batch_desc* desc, vie_batch** out);
+
+/* Waits for the device, then frees the batch and its cached spectra. */
+int vie_batch_destroy(vie_batch* batch);
+
+/* Solves A_i E_i = E_inc,i for every instance i at wavenumber k0s[i] (HOST,
+ * count doubles; spectra are computed in FP64 per distinct value and cached in
+ * the batch). Mixed precision only (opts->mode = VIE_MODE_MIXED): FP64 true
+ * residuals of all instances from one batched complex128 MVM, then one
+ * complex64 correction solve for every instance still above outer_tol, all in
+ * one persistent launch (one CTA cluster per instance) when the padded plane
+ * fits in shared memory, else batched launches per BiCGSTAB step; E += d.
+ * outer_maxit bounds each correction; inner_tol, inner_maxit and use_precond
+ * are ignored (no blocks). einc_dev, e_dev: DEVICE complex128
+ * [count][3][nz][ny][nx], distinct. stats: NULL or count entries
+ * (outer_iters = correction iterations summed over refinements).
+ * Returns VIE_OK when every instance meets outer_tol, VIE_ENOTCONV otherwise
+ * (all outputs valid), VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA, VIE_ETIMEOUT. */
+int vie_batch_solve(vie_batch* batch, const double* k0s, const void* einc_dev,
+                    void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
+                    vie_solve_stats* stats);
+
+/* Device bytes held by the batch (with its cached spectra), and whether its
+ * corrections run in the persistent kernel (1) or in batched launches (0). */
+int vie_batch_get_info(const vie_batch* batch, int64_t* device_bytes, int32_t* persistent);
+
 /* Kernel-level profile, aggregated per kernel kind and precision. */
 typedef struct {
     char name[32];           /* x_fwd, y_fwd, z_green, y_inv, x_inv, bicg_update,

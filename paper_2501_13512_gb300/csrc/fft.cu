@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_cols(ColArgs<C> a) {
 template <class C> struct ZArgs {
     C* w;                 // w2 of the BoxSet
     const C* G;           // [6][Mz][My][Mx]
+    const C* const* Gb;   // optional: one spectrum per box (instances with their own wavenumber)
     const SegState* st;
     const C* tw;
     int ncols, nzb, lL, ltc, twshift;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) k_zgreen(ZArgs<C> a) {
     for (int idx = threadIdx.x; idx < L * TC; idx += blockDim.x) {
         int c = idx & (TC - 1), i = idx >> a.ltc;
         if (c >= ncol) continue;
-        const C* g = a.G + i * a.axis + col0 + c;
+        const C* g = (a.Gb ? a.Gb[b] : a.G) + i * a.axis + col0 + c;
         C gxx = g[0], gxy = g[a.gcomp], gxz = g[2 * a.gcomp];
         C gyy = g[3 * a.gcomp], gyz = g[4 * a.gcomp], gzz = g[5 * a.gcomp];
         C* p = buf + i * pitch + c;
@@ -287,7 +288,7 @@ template <> const float2* chi_ptr<float2>(const BoxSet& bs) { return bs.chi64; }
 
 template <class C>
 int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st, cudaStream_t s,
-              const Twiddles* twp) {
+              const Twiddles* twp, const C* const* Gb) {
     Twiddles tw;
     if (twp) tw = *twp;
     else VIE_TRY(get_twiddles(&tw));
@@ -328,7 +329,7 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
 
     // pass Z: forward, Green multiply, inverse
     ZArgs<C> z{};
-    z.w = w2; z.G = G; z.st = st; z.tw = T;
+    z.w = w2; z.G = G; z.Gb = Gb; z.st = st; z.tw = T;
     z.ncols = (int)planeXY; z.nzb = bs.bz; z.lL = bs.lz; z.twshift = kLogLmax - bs.lz;
     z.axis = planeXY; z.comp_stride = (int64_t)bs.bz * planeXY; z.box_stride = 3 * z.comp_stride;
     z.gcomp = (int64_t)bs.Mz * planeXY;
@@ -386,9 +387,9 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* twp) {
 }
 
 template int mvm_boxes<double2>(const BoxSet&, const double2*, const double2*, double2*, const SegState*, cudaStream_t,
-                                const Twiddles*);
+                                const Twiddles*, const double2* const*);
 template int mvm_boxes<float2>(const BoxSet&, const float2*, const float2*, float2*, const SegState*, cudaStream_t,
-                               const Twiddles*);
+                               const Twiddles*, const float2* const*);
 template int spectrum_fft<double2>(const BoxSet&, double2*, cudaStream_t, const Twiddles*);
 
 }  // namespace vie

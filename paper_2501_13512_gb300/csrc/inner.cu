@@ -38,6 +38,8 @@ template <class C> struct InnerGroup {
     const C* chi;                           // [nb][bz][by][bx]
     const uint8_t* mask;                    // [nb][bz][by][bx]
     const C* G;                             // [6][Mz][My][Mx], bit-reversed positions
+    const C* const* Gb;                     // optional: one spectrum per box
+    const double* tols;                     // optional: one relative tolerance per box
     SegState* st;                           // [nb]
     int nb, bx, by, bz, Mx, My, Mz, lx, ly, lz, lyb;   // lyb = log2 of nextpow2(by)
     int lpt;                                // log2 planes per XY tile
@@ -906,9 +908,12 @@ __global__ void __launch_bounds__(kInnerThreads, 2) k_inner(const InnerGroup<C>*
         const int2 wk = work[it];
         // descriptor in shared memory: fields are reloaded after barriers instead of held in registers
         __shared__ InnerGroup<C> gsh;
-        if (threadIdx.x == 0) gsh = groups[wk.x];
+        if (threadIdx.x == 0) {
+            gsh = groups[wk.x];
+            if (gsh.Gb) gsh.G = gsh.Gb[wk.y];
+        }
         __syncthreads();
-        solve_dispatch(gsh, wk.y, tol, maxit, sm, tw, red, units);
+        solve_dispatch(gsh, wk.y, gsh.tols ? gsh.tols[wk.y] : tol, maxit, sm, tw, red, units);
         __syncthreads();
     }
 }
@@ -1000,6 +1005,8 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         g.chi = j.chi;
         g.mask = bs.mask;
         g.G = j.G;
+        g.Gb = j.Gb;
+        g.tols = j.tols;
         g.st = j.st;
         g.nb = bs.nb; g.bx = bs.bx; g.by = bs.by; g.bz = bs.bz;
         g.Mx = bs.Mx; g.My = bs.My; g.Mz = bs.Mz; g.lx = bs.lx; g.ly = bs.ly; g.lz = bs.lz;

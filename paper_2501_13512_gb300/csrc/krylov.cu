@@ -32,6 +32,7 @@ template <class C> struct VecArgs {
     double tol;
     int maxit;
     int* units;         // profiling: active segments processed
+    const double* tols; // optional per-segment relative tolerance (OP_INIT)
 };
 
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
@@ -89,6 +90,7 @@ __device__ __forceinline__ void leave_active(int* n_active) { atomicSub(n_active
 // Scalar update of one segment, run by thread 0 of the last CTA.
 template <int OP>
 __device__ void finalize(SegState& s, double2 d1, double2 d2, int* n_active, double tol, int maxit) {
+    // (tol already resolved per segment by the caller)
     if (OP == OP_INIT) {
         s.bnorm2 = d1.x;
         s.tol2 = tol * tol * d1.x;
@@ -211,13 +213,14 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg(VecArgs<C> a) {
     block_sum2(s1, s2);
     if (threadIdx.x == 0) {
         a.count[seg] = 0;
-        finalize<OP>(S, s1, s2, a.n_active, a.tol, a.maxit);
+        finalize<OP>(S, s1, s2, a.n_active, a.tols ? a.tols[seg] : a.tol, a.maxit);
     }
 }
 
 template <class C>
-static int launch_bicg(Bicg<C>& k, int op, double tol, int maxit, cudaStream_t s) {
+static int launch_bicg(Bicg<C>& k, int op, double tol, int maxit, cudaStream_t s, const double* tols = nullptr) {
     VecArgs<C> a;
+    a.tols = tols;
     a.v = k.v;
     a.st = k.st;
     a.part = k.red->part;
@@ -255,6 +258,10 @@ template <class C> int bicg_init(Bicg<C>& k, double tol, int maxit, cudaStream_t
     VIE_CK(cudaMemsetAsync(k.red->n_active, 0, sizeof(int), s));
     return launch_bicg(k, OP_INIT, tol, maxit, s);
 }
+template <class C> int bicg_init_tols(Bicg<C>& k, const double* tols, int maxit, cudaStream_t s) {
+    VIE_CK(cudaMemsetAsync(k.red->n_active, 0, sizeof(int), s));
+    return launch_bicg(k, OP_INIT, 0.0, maxit, s, tols);
+}
 template <class C> int bicg_rho(Bicg<C>& k, cudaStream_t s) { return launch_bicg(k, OP_RHO, 0, 0, s); }
 template <class C> int bicg_update_p(Bicg<C>& k, cudaStream_t s) { return launch_bicg(k, OP_P, 0, 0, s); }
 template <class C> int bicg_sigma(Bicg<C>& k, cudaStream_t s) { return launch_bicg(k, OP_SIGMA, 0, 0, s); }
@@ -265,6 +272,7 @@ template <class C> int bicg_update_xr(Bicg<C>& k, cudaStream_t s) { return launc
 
 #define VIE_INST(C)                                                        \
     template int bicg_init<C>(Bicg<C>&, double, int, cudaStream_t);        \
+    template int bicg_init_tols<C>(Bicg<C>&, const double*, int, cudaStream_t); \
     template int bicg_rho<C>(Bicg<C>&, cudaStream_t);                      \
     template int bicg_update_p<C>(Bicg<C>&, cudaStream_t);                 \
     template int bicg_sigma<C>(Bicg<C>&, cudaStream_t);                    \

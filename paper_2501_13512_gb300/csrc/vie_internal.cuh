@@ -194,9 +194,10 @@ void prof_end(cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers (fft.cu)
 // tw: twiddle tables to use; null = the per-device tables of get_twiddles()
+// Gb: optional device array of one spectrum pointer per box (null: G for every box)
 template <class C>
 int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st,
-              cudaStream_t s, const Twiddles* tw = nullptr);
+              cudaStream_t s, const Twiddles* tw = nullptr, const C* const* Gb = nullptr);
 template <class C>
 int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* tw = nullptr);   // in place, 6 components
 
@@ -216,6 +217,7 @@ struct Bicg {
     ReduceScratch* red;
 };
 template <class C> int bicg_init(Bicg<C>& k, double tol, int maxit, cudaStream_t s);
+template <class C> int bicg_init_tols(Bicg<C>& k, const double* tols, int maxit, cudaStream_t s);
 template <class C> int bicg_rho(Bicg<C>& k, cudaStream_t s);
 template <class C> int bicg_update_p(Bicg<C>& k, cudaStream_t s);
 template <class C> int bicg_sigma(Bicg<C>& k, cudaStream_t s);
@@ -240,6 +242,8 @@ template <class C> struct InnerJob {
     const C* chi;
     const C* G;
     SegState* st;
+    const C* const* Gb = nullptr;   // optional device array: one spectrum per box
+    const double* tols = nullptr;   // optional device array: one relative tolerance per box
 };
 bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force);
 size_t inner_group_desc_bytes();

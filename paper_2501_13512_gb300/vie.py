@@ -59,6 +59,11 @@ class SolveStats(ctypes.Structure):
                 ("true_rel_res", c_double), ("status", c_int32)]
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("h", c_double), ("count", c_int32),
+                ("eps_r", POINTER(c_double)), ("flags", c_uint32)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("precision", c_int32), ("launches", c_int64),
                 ("total_ms", c_double), ("bytes", c_double)]
@@ -99,6 +104,10 @@ def load(path=LIB_PATH):
         "vie_block_precond_apply": ([P, P, c_int, P, P, c_double, c_int, P, POINTER(PrecondStats)], c_int),
         "vie_solve": ([P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
         "vie_matvec_noalloc": ([c_int32, c_int32, c_int32, c_double, c_double, P, P, P, P], c_int),
+        "vie_batch_create": ([POINTER(BatchDesc), POINTER(P)], c_int),
+        "vie_batch_destroy": ([P], c_int),
+        "vie_batch_solve": ([P, POINTER(c_double), P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
+        "vie_batch_get_info": ([P, POINTER(c_int64), POINTER(c_int32)], c_int),
         "vie_profile_enable": ([c_int], c_int),
         "vie_profile_read": ([POINTER(KernelStat), c_int, POINTER(c_int), POINTER(c_int64)], c_int),
     }
@@ -280,3 +289,54 @@ class Grid:
         out_host.copy_(e, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return out_host, st
+
+
+class Batch:
+    """Independent instances of one grid shape solved together (vie_batch)."""
+
+    def __init__(self, eps_list, h):
+        lib = load()
+        eps = np.ascontiguousarray(np.stack([np.asarray(e, dtype=np.complex128) for e in eps_list]))
+        self.count, nz, ny, nx = eps.shape
+        self.shape = (nz, ny, nx)
+        self._eps = eps.view(np.float64).reshape(-1)
+        d = BatchDesc(nx, ny, nz, float(h), self.count, self._eps.ctypes.data_as(POINTER(c_double)), 0)
+        handle = c_void_p()
+        _check(lib.vie_batch_create(byref(d), byref(handle)))
+        self.handle = handle
+
+    def info(self):
+        nbytes, pers = c_int64(), c_int32()
+        _check(load().vie_batch_get_info(self.handle, byref(nbytes), byref(pers)))
+        return {"device_bytes": nbytes.value, "persistent": bool(pers.value)}
+
+    def empty(self):
+        import torch
+        return torch.empty((self.count, 3) + self.shape, dtype=torch.complex128, device="cuda")
+
+    def solve(self, k0s, einc, e=None, outer_tol=1e-6, outer_maxit=1000, max_refinements=0, wait_timeout_ms=0.0,
+              check=True):
+        import torch
+        if tuple(einc.shape) != (self.count, 3) + self.shape or einc.dtype != torch.complex128 or not einc.is_cuda:
+            raise ValueError("einc must be a complex128 CUDA tensor of shape (count, 3, nz, ny, nx)")
+        e = self.empty() if e is None else e
+        k = (c_double * self.count)(*[float(v) for v in np.broadcast_to(np.asarray(k0s, float), (self.count,))])
+        o = SolveOpts(float(outer_tol), 0.0, int(outer_maxit), 1, 0, MODE_MIXED, int(max_refinements),
+                      float(wait_timeout_ms))
+        st = (SolveStats * self.count)()
+        rc = load().vie_batch_solve(self.handle, k, c_void_p(einc.data_ptr()), c_void_p(e.data_ptr()), byref(o),
+                                    _stream(), st)
+        if check:
+            _check(rc, allow=(VIE_ENOTCONV,))
+        return e, [_struct_dict(x) for x in st]
+
+    def close(self):
+        if self.handle:
+            _check(load().vie_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
