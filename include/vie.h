@@ -115,8 +115,11 @@ int vie_grid_get_info(const vie_grid* grid, vie_grid_info* info);
  * computes in FP64 on the device the 3D FFT of the six components of K for
  * the full grid and for every block group, at wavenumber k0 > 0.
  * precision_mask: VIE_C128, VIE_C64 or both (bitwise or); the complex64 copy
- * is rounded from the FP64 spectrum. The spectrum belongs to the grid and must
- * be released before the grid is destroyed. Asynchronous on `stream`.
+ * is rounded from the FP64 spectrum. The spectrum is owned by the caller and
+ * serves the grid it was made for and every other grid with the same h, padded
+ * shapes and block-group box extents (e.g. the same structure created twice);
+ * it must be released before the grid it was made for is destroyed.
+ * Asynchronous on `stream`.
  * Errors: VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA. */
 int vie_green_spectrum(vie_grid* grid, double k0, int precision_mask,
                        vie_stream_t stream, vie_spectrum** out);

@@ -387,6 +387,10 @@ extern "C" int vie_grid_get_info(const vie_grid* g, vie_grid_info* info) {
 }
 
 // ---------------------------------------------------------------- spectra
+namespace vie {
+static std::vector<int> shape_signature(const vie_grid* g);
+}
+
 extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t stream, vie_spectrum** out) {
     if (!g || !out) return fail(VIE_EINVAL, "vie_green_spectrum: null argument");
     *out = nullptr;
@@ -395,6 +399,8 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
     cudaStream_t s = (cudaStream_t)stream;
     vie_spectrum* sp = new vie_spectrum();
     sp->grid = g;
+    sp->h = g->h;
+    sp->shape_sig = shape_signature(g);
     sp->k0 = k0;
     sp->precision_mask = mask;
     auto bail = [&](int rc) {
@@ -468,8 +474,27 @@ template <class C> static int prec_of();
 template <> int prec_of<double2>() { return VIE_C128; }
 template <> int prec_of<float2>() { return VIE_C64; }
 
+// A spectrum depends only on h, the padded shapes and the box extents of the
+// grid and of its block groups, so it serves every grid that matches them.
+static std::vector<int> shape_signature(const vie_grid* g) {
+    std::vector<int> v;
+    auto add = [&](const BoxSet& x) {
+        int a[6] = {x.bx, x.by, x.bz, x.Mx, x.My, x.Mz};
+        v.insert(v.end(), a, a + 6);
+    };
+    add(g->full);
+    for (const auto& gr : g->groups) add(gr.bs);
+    return v;
+}
+
+static bool spectrum_compatible(const vie_spectrum* sp, const vie_grid* g) {
+    // compared by value: the address of a destroyed grid may be reused by a new one
+    return sp->h == g->h && sp->shape_sig == shape_signature(g);
+}
+
 static int check_spectrum(const vie_grid* g, const vie_spectrum* sp, int precision) {
-    if (!sp || sp->grid != g) return fail(VIE_EINVAL, "spectrum does not belong to this grid");
+    if (!sp || !spectrum_compatible(sp, g))
+        return fail(VIE_EINVAL, "spectrum was made for a grid of another shape, block layout or voxel size");
     if (precision != VIE_C128 && precision != VIE_C64) return fail(VIE_EINVAL, "precision must be VIE_C128 or VIE_C64");
     if (!(sp->precision_mask & precision)) return fail(VIE_EINVAL, "spectrum was not generated in this precision");
     return VIE_OK;

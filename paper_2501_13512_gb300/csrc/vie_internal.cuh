@@ -134,7 +134,11 @@ struct Group {
 }  // namespace vie
 
 struct vie_spectrum {
-    vie_grid* grid = nullptr;
+    vie_grid* grid = nullptr;             // the grid it was made for (identity only, never dereferenced)
+    // what the spectrum depends on: h and (box extents, padded shape) of the
+    // full grid and of every block group; any grid matching it may use it
+    double h = 0.0;
+    std::vector<int> shape_sig;
     double k0 = 0.0;
     int precision_mask = 0;
     // index 0: full grid; 1 + g: group g. Layout [6][Mz][My][Mx] (bit-reversed
