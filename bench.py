@@ -44,6 +44,12 @@ def parse():
     ap.add_argument("--plain-iters", type=int, default=3,
                     help="outer iterations of the plain FP64 solve to time (it needs hundreds to converge)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--serve", type=int, default=8, help="requests in the serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-sizes", default="32,64", help="cubic grid sizes of the serving stream")
+    ap.add_argument("--serve-kinds", default="metasurface",
+                    help="structures of the serving stream: metasurface and/or solar_cell (comma separated)")
+    ap.add_argument("--batch", type=int, default=64, help="instances in the batched-solve run (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     return ap.parse_args()
@@ -184,6 +190,23 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- our arm
+def traffic_per_launch(kernel, algorithmic_bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu capture of `kernel`, scaled by the
+    algorithmic bytes of the bench's average launch; None if the kernel source changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    h = hashlib.sha256()
+    for src in rec["kernel_sources"]:
+        h.update(open(os.path.join(ROOT, src), "rb").read())
+    if h.hexdigest() != rec["kernel_sources_sha256"]:
+        return None
+    dram = rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    return dram * algorithmic_bytes_per_launch / rec["algorithmic_bytes_same_launch"]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -351,8 +374,9 @@ def main():
         per_launch_ms = dom["total_ms"] / dom["launches"]
         bytes_per_launch = dom["bytes"] / dom["launches"]
         ach = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+        kname = f"{dom['name']}_{dom['precision']}"
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "kernel": f"{dom['name']}_{dom['precision']}",
+                "traffic": traffic_per_launch(kname, bytes_per_launch), "kernel": kname,
                 "launches": dom["launches"], "ms_per_launch": per_launch_ms,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "share_of_kernel_time": dom["total_ms"] / tot,
                 "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
@@ -361,6 +385,65 @@ def main():
                    for k in sorted(kstats, key=lambda k: -k["total_ms"])}
     else:
         kernels = None
+
+    # serving: Poisson arrivals, continuous batching over slots (p50/p99 latency)
+    serving = None
+    if args.serve > 0:
+        from paper_2501_13512_gb300 import serve
+        sizes = tuple(int(v) for v in args.serve_sizes.split(","))
+        wts = [serve.SIZE_WEIGHTS[serve.SIZES.index(n)] if n in serve.SIZES else 1.0 for n in sizes]
+        kinds = tuple(args.serve_kinds.split(","))
+        reqs = serve.make_stream(args.serve, seed=rank, sizes=sizes, weights=wts, kinds=kinds, outer_maxit=400)
+        for r in reqs:
+            r.want_field = False
+        srv = serve.Server(budget_bytes=int(0.5 * torch.cuda.get_device_properties(0).total_memory), slots=4)
+        rng = np.random.default_rng(1 + rank)
+        futs = []
+        t0 = time.perf_counter()
+        try:
+            for r in reqs:
+                futs.append(srv.submit(r))
+                time.sleep(rng.exponential(1.0 / args.serve_rate))
+            res = [f.result(timeout=600) for f in futs]
+        finally:
+            srv.close()
+        slat = np.array([x.latency_s for x in res])
+        st = srv.latency_stats()
+        serving = {"requests": len(res), "arrival_rate": args.serve_rate, "sizes": list(sizes), "slots": 4,
+                   "p50_s": float(np.percentile(slat, 50)), "p99_s": float(np.percentile(slat, 99)),
+                   "solves_per_s": st["solves_per_s"],
+                   "converged": int(sum(x.stats["status"] == 0 for x in res)),
+                   "max_true_rel_res": float(max(x.stats["true_rel_res"] for x in res)),
+                   "cache": dict(srv.engine.hits),
+                   "workload": f"{'/'.join(kinds)} structures on n^3 grids, h = 10 nm, wavelengths 400-800 nm "
+                               "(10 nm grid), random incidence; mixed, outer 1e-6, inner 1e-2, outer_maxit 400"}
+
+    # batched independent solves: blob instances of several sizes, one persistent launch per size
+    batched = None
+    if args.batch > 0:
+        per = max(1, args.batch // 4)
+        tot_s, tot_n, per_size = 0.0, 0, {}
+        for n in (16, 24, 32, 48):
+            ws = [inputs.blob(n=n, seed=1000 * n + i) for i in range(per)]
+            b = vie.Batch([wi.eps_r for wi in ws], ws[0].h)
+            gpw = [vie.Grid(wi.eps_r, wi.h) for wi in ws[:1]]
+            ein = torch.stack([gpw[0].plane_wave(wi.k0, wi.khat, wi.pol) for wi in ws])
+            b.solve([wi.k0 for wi in ws], ein)                      # warm-up (spectra built, kernels loaded)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, bst = b.solve([wi.k0 for wi in ws], ein)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            per_size[f"{n}^3"] = {"instances": per, "s": dt, "persistent": b.info()["persistent"],
+                                  "mean_correction_iters": float(np.mean([x["outer_iters"] for x in bst])),
+                                  "max_true_rel_res": float(max(x["true_rel_res"] for x in bst))}
+            tot_s += dt
+            tot_n += per
+            b.close()
+            gpw[0].close()
+        batched = {"instances": tot_n, "solves_per_s": tot_n / tot_s, "per_size": per_size,
+                   "workload": "smoothed random blobs, eps_r U[2,8], random incidence, h = lambda0/20; "
+                               "mixed, outer 1e-6, unpreconditioned"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -378,13 +461,14 @@ def main():
             "config": config({"parallelism": "replicas" if world > 1 else "single GPU"}),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "mvm_per_s": {"c64": mvm64 * world, "c128": mvm128 * world},
-            "solve": {"outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
+            "solve": {"inner_cluster_tuned": g.info()["inner_cluster"][1],
+                      "outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
                       "precond_applies": last["precond_applies"], "matvecs_c128": last["matvecs_c128"],
                       "matvecs_c64": last["matvecs_c64"], "refinements": last["refinements"],
                       "true_rel_res": last["true_rel_res"]},
             "plain_c128": plain, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "roofline_full_grid_mvm": roof_mvm, "kernels": kernels, "clocks": clocks,
-            "cpu_baseline": cpu}
+            "serving": serving, "batched": batched, "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

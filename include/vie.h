@@ -96,6 +96,8 @@ typedef struct {
     int32_t ngroups;         /* batches of blocks sharing one padded FFT shape     */
     int32_t Mx, My, Mz;      /* padded FFT shape of the full-grid operator         */
     int64_t device_bytes;    /* device memory held by the grid handle              */
+    int32_t inner_cluster[2];/* CTAs per block chosen by the block solver's tuner for
+                                complex128 [0] and complex64 [1]; 0 = not yet tuned  */
 } vie_grid_info;
 
 /* Creates the grid on the current CUDA device: uploads chi = eps_r - 1,

@@ -159,8 +159,10 @@ static void release_grid(vie_grid* g) {
     for (void* p : g->allocations) cudaFree(p);
     g->allocations.clear();
     if (g->h_ring) cudaFreeHost(g->h_ring);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+        if (g->tev[i]) cudaEventDestroy(g->tev[i]);
+    }
     delete g;
 }
 
@@ -358,7 +360,8 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
     if (cudaHostAlloc((void**)&g->h_ring, ring, cudaHostAllocDefault) != cudaSuccess)
         return bail(fail(VIE_ENOMEM, "pinned host allocation failed"));
     for (int i = 0; i < 2; ++i)
-        if (cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming) != cudaSuccess)
+        if (cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&g->tev[i]) != cudaSuccess)
             return bail(fail(VIE_ECUDA, "cudaEventCreate failed"));
     *out = g;
     return VIE_OK;
@@ -383,6 +386,8 @@ extern "C" int vie_grid_get_info(const vie_grid* g, vie_grid_info* info) {
     info->My = g->full.My;
     info->Mz = g->full.Mz;
     info->device_bytes = g->device_bytes;
+    info->inner_cluster[0] = g->tune_best[0];
+    info->inner_cluster[1] = g->tune_best[1];
     return VIE_OK;
 }
 
@@ -539,8 +544,16 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             batched.push_back(i);
         }
     }
+    // cluster size: candidates 2 and 4 tried on the first two applies, then the best
+    static const int kCand[2] = {2, 4};
+    const int pi = c128 ? 0 : 1;
+    const int tried = g->tune_count[pi];
+    const bool tuning = !jobs.empty() && tried < 2 && !inner_cluster_forced();
+    const int R = tuning ? kCand[tried] : (g->tune_best[pi] ? g->tune_best[pi] : 2);
+    if (tuning) VIE_CK(cudaEventRecord(g->tev[0], s));
     VIE_TRY(inner_persistent<C>(jobs, c128 ? g->work128 : g->work64, c128 ? g->nwork128 : g->nwork64,
-                                g->inner_groups, g->inner_next, tol, maxit, s));
+                                g->inner_groups, g->inner_next, tol, maxit, s, R));
+    if (tuning) VIE_CK(cudaEventRecord(g->tev[1], s));
     std::vector<Bicg<C>> bk(ng);
     for (int i : batched) {
         Group& gr = g->groups[i];
@@ -600,6 +613,21 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             }
         }
         stats->mean_iters = sum / std::max(1, g->nblocks);
+    }
+    if (tuning) {
+        // score: persistent-launch time per iteration of its slowest block (the critical path)
+        VIE_TRY(wait_event(g->tev[1], timeout_ms));
+        float ms = 0.f;
+        VIE_CK(cudaEventElapsedTime(&ms, g->tev[0], g->tev[1]));
+        int maxit_seen = 1;
+        std::vector<SegState> hs;
+        for (auto& gr : g->groups) {
+            hs.resize(gr.bs.nb);
+            VIE_CK(cudaMemcpy(hs.data(), gr.st, gr.bs.nb * sizeof(SegState), cudaMemcpyDeviceToHost));
+            for (auto& st : hs) maxit_seen = std::max(maxit_seen, (int)std::ceil(st.iters));
+        }
+        g->tune_score[pi][tried] = ms / maxit_seen;
+        if (++g->tune_count[pi] == 2) g->tune_best[pi] = g->tune_score[pi][1] < g->tune_score[pi][0] ? kCand[1] : kCand[0];
     }
     return VIE_OK;
 }

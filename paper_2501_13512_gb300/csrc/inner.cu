@@ -927,13 +927,13 @@ static int lg2(int v) {
 
 constexpr size_t kInnerSmemBudget = 96 * 1024;
 
-// CTAs per block (thread-block cluster size) of the persistent solver: 1, 2, 4 or 8.
-// Default 2; the environment variable VIE_INNER_CLUSTER overrides it (read once).
-static int inner_cluster_size() {
+// CTAs per block (thread-block cluster size) forced by the environment variable
+// VIE_INNER_CLUSTER (1, 2, 4 or 8; read once), or 0 when unset.
+int inner_cluster_forced() {
     static const int r = [] {
         const char* e = getenv("VIE_INNER_CLUSTER");
-        int v = e ? atoi(e) : 2;
-        return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 2;
+        int v = e ? atoi(e) : 0;
+        return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
     }();
     return r;
 }
@@ -988,7 +988,7 @@ bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force) {
 
 template <class C>
 int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, int nwork, void* d_groups,
-                     int* d_next, double tol, int maxit, cudaStream_t s) {
+                     int* d_next, double tol, int maxit, cudaStream_t s, int cluster) {
     if (jobs.empty() || nwork == 0) return VIE_OK;
     Twiddles tw;
     VIE_TRY(get_twiddles(&tw));
@@ -1045,7 +1045,7 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
     // opt in to the exact dynamic size: the default 48 KB limit also counts the static shared memory
     VIE_CK(cudaFuncSetAttribute(k_inner<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // one block per cluster of R CTAs; as many clusters as fit at once, pulling blocks from the queue
-    const int R = inner_cluster_size();
+    const int R = inner_cluster_forced() ? inner_cluster_forced() : (cluster > 0 ? cluster : 2);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = R;
@@ -1076,9 +1076,9 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
 }
 
 template int inner_persistent<double2>(const std::vector<InnerJob<double2>>&, const int2*, int, void*, int*, double,
-                                       int, cudaStream_t);
+                                       int, cudaStream_t, int);
 template int inner_persistent<float2>(const std::vector<InnerJob<float2>>&, const int2*, int, void*, int*, double, int,
-                                      cudaStream_t);
+                                      cudaStream_t, int);
 
 size_t inner_group_desc_bytes() { return std::max(sizeof(InnerGroup<double2>), sizeof(InnerGroup<float2>)); }
 

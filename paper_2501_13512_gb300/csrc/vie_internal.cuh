@@ -175,6 +175,12 @@ struct vie_grid {
     int nwork128 = 0, nwork64 = 0;
     void* inner_groups = nullptr;         // device copy of the per-group descriptors
     int* inner_next = nullptr;            // work counter
+    // cluster-size autotuning of the persistent solver, per precision (0: c128, 1: c64):
+    // applies 0 and 1 try the candidates, later applies use the best
+    int tune_count[2] = {0, 0};
+    int tune_best[2] = {0, 0};
+    double tune_score[2][2] = {{0, 0}, {0, 0}};
+    cudaEvent_t tev[2] = {nullptr, nullptr};
     int64_t device_bytes = 0;
     std::vector<void*> allocations;
 };
@@ -251,9 +257,11 @@ template <class C> struct InnerJob {
 };
 bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force);
 size_t inner_group_desc_bytes();
+// cluster: CTAs per block (1, 2, 4, 8; 0 = 2), unless VIE_INNER_CLUSTER forces one
 template <class C>
 int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, int nwork, void* d_groups,
-                     int* d_next, double tol, int maxit, cudaStream_t s);
+                     int* d_next, double tol, int maxit, cudaStream_t s, int cluster = 0);
+int inner_cluster_forced();
 template <class C> inline const C* tw_of(const Twiddles& t);
 template <> inline const double2* tw_of<double2>(const Twiddles& t) { return t.d128; }
 template <> inline const float2* tw_of<float2>(const Twiddles& t) { return t.d64; }

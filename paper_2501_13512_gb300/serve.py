@@ -280,12 +280,13 @@ class Server:
                     self.done.append(req)
                     self.cv.notify_all()
 
-    def close(self):
+    def close(self, timeout=None):
+        """Stop taking work and wait for the running solves (each is bounded by its outer_maxit)."""
         with self.cv:
             self.stop = True
             self.cv.notify_all()
         for t in self.workers:
-            t.join(timeout=60)
+            t.join(timeout=timeout)
 
     def latency_stats(self):
         lat = np.array([r.t_done - r.t_submit for r in self.done if r.t_done > 0])
@@ -303,7 +304,8 @@ SIZE_WEIGHTS = (0.4, 0.3, 0.2, 0.1)
 WAVELENGTHS_NM = tuple(range(400, 801, 10))
 
 
-def make_stream(nreq, seed=0, sizes=SIZES, weights=SIZE_WEIGHTS, h_nm=10.0, structures_per_size=2):
+def make_stream(nreq, seed=0, sizes=SIZES, weights=SIZE_WEIGHTS, h_nm=10.0, structures_per_size=2,
+                kinds=("metasurface", "solar_cell"), outer_maxit=1000):
     """Serving workload: grids drawn from `sizes`, structures alternating metasurface
     tiles and particle slabs rescaled to n, wavelength from a 10 nm sweep grid,
     random incidence angle (x-polarised plane waves tilted in the xz plane)."""
@@ -313,7 +315,7 @@ def make_stream(nreq, seed=0, sizes=SIZES, weights=SIZE_WEIGHTS, h_nm=10.0, stru
     out = []
     for i in range(nreq):
         n = int(rng.choice(sizes, p=np.asarray(weights) / np.sum(weights)))
-        kind = "metasurface" if (i % 2 == 0) else "solar_cell"
+        kind = kinds[i % len(kinds)]
         sid = int(rng.integers(structures_per_size))
         key = f"{kind}-{n}-{sid}"
         if key not in geo:
@@ -330,5 +332,5 @@ def make_stream(nreq, seed=0, sizes=SIZES, weights=SIZE_WEIGHTS, h_nm=10.0, stru
         khat = np.array([np.sin(th), 0.0, np.cos(th)])
         pol = np.array([np.cos(th), 0.0, -np.sin(th)], complex)
         out.append(Request(structure=key, eps_r=w.eps_r, h=h_nm, k0=2 * np.pi / lam, khat=khat, pol=pol,
-                           block_id=w.block_id))
+                           block_id=w.block_id, outer_maxit=outer_maxit))
     return out

@@ -39,7 +39,7 @@ class GridDesc(ctypes.Structure):
 
 class GridInfo(ctypes.Structure):
     _fields_ = [("nblocks", c_int32), ("ngroups", c_int32), ("Mx", c_int32), ("My", c_int32),
-                ("Mz", c_int32), ("device_bytes", c_int64)]
+                ("Mz", c_int32), ("device_bytes", c_int64), ("inner_cluster", c_int32 * 2)]
 
 
 class PrecondStats(ctypes.Structure):
@@ -213,7 +213,9 @@ class Grid:
     def info(self):
         inf = GridInfo()
         _check(load().vie_grid_get_info(self.handle, byref(inf)))
-        return _struct_dict(inf)
+        d = _struct_dict(inf)
+        d["inner_cluster"] = list(inf.inner_cluster)
+        return d
 
     def close(self):
         if self.handle:
