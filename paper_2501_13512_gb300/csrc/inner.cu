@@ -98,24 +98,33 @@ __device__ __forceinline__ int team_rank() { return (int)cg::this_cluster().bloc
 __device__ __forceinline__ int team_size() { return (int)cg::this_cluster().num_blocks(); }
 __device__ __forceinline__ void team_sync() { cg::this_cluster().sync(); }
 
+// Slot of the next cluster sum; reset to 0 by every CTA at kernel entry so all
+// ranks of a cluster flip in step.
+__shared__ int team_slot;
+
+// Two slots alternate between consecutive sums: a slot is rewritten two sums
+// later, after every rank has passed the barrier of the sum in between (by
+// which time all reads of the slot are done), so one barrier per sum suffices.
 __device__ void team_sum2(double2& a, double2& b, double2* red) {
     cta_sum2(a, b, red);
     cg::cluster_group cl = cg::this_cluster();
     const unsigned R = cl.num_blocks();
     if (R == 1) return;
-    __shared__ double2 xred[2];
+    __shared__ double2 xred[2][2];
+    if (threadIdx.x == 0) team_slot ^= 1;  // every rank flips in step (same call sequence)
+    __syncthreads();
+    const int sl = team_slot;
     if (threadIdx.x == 0) {
-        xred[0] = a;
-        xred[1] = b;
+        xred[sl][0] = a;
+        xred[sl][1] = b;
     }
     cl.sync();
     double2 sa = make_double2(0, 0), sb = make_double2(0, 0);
     for (unsigned r = 0; r < R; ++r) {
-        const double2* q = cl.map_shared_rank(xred, r);
+        const double2* q = cl.map_shared_rank(&xred[sl][0], r);
         sa.x += q[0].x; sa.y += q[0].y;
         sb.x += q[1].x; sb.y += q[1].y;
     }
-    cl.sync();
     a = sa;
     b = sb;
 }
@@ -167,9 +176,7 @@ __device__ double2 phase_xy(const InnerGroup<C>& g, int64_t voff, C* W, const C*
         }
         __syncthreads();
     }
-    double2 a = wide<C>(acc), z = make_double2(0, 0);
-    team_sum2(a, z, red);
-    return a;
+    return wide<C>(acc);   // this thread's partial; the caller folds it into a later sum
 }
 
 // Phase Z: forward FFT along z, Green multiply, inverse FFT (columns of the plane spectra).
@@ -217,7 +224,7 @@ __device__ void phase_z(const InnerGroup<C>& g, C* W, C* sm, const C* tw) {
 // OUT_V: in = p, out = v, returns <rhat, v>.  OUT_T: in = s, out = t, returns (<t, s>, <t, t>).
 template <class C, int OUT>
 __device__ void phase_xy_inv(const InnerGroup<C>& g, int64_t voff, const C* W, const uint8_t* mask, C* sm,
-                             const C* tw, double2* red, double2& d1, double2& d2) {
+                             const C* tw, double2* red, double2& d1, double2& d2, double extra) {
     const int planes = 3 * g.bz, P = g.Mx + 1, pe = g.My * P, tile = 1 << g.lpt;
     const int64_t box = (int64_t)g.bx * g.by * g.bz;
     C a1 = czero<C>(), a2 = czero<C>();
@@ -258,6 +265,7 @@ __device__ void phase_xy_inv(const InnerGroup<C>& g, int64_t voff, const C* W, c
     }
     d1 = wide<C>(a1);
     d2 = wide<C>(a2);
+    d2.y = extra;          // deferred sum (||s||^2) rides in the unused imaginary slot
     team_sum2(d1, d2, red);
 }
 
@@ -273,6 +281,9 @@ __device__ __forceinline__ C twmul(C v, int m, const C* __restrict__ tw) {
     C w = __ldg(&tw[m]);
     return FWD ? cmul(v, w) : cmulc(v, w);
 }
+
+template <int L> struct ILog2 { static constexpr int v = 1 + ILog2<L / 2>::v; };
+template <> struct ILog2<1> { static constexpr int v = 0; };
 
 // Twiddle multiply used by the register FFTs (specialised below per precision).
 template <class C> struct TwSel;
@@ -353,6 +364,13 @@ struct FastDiv {
 };
 __device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv f) { return (__umulhi(n, f.m) + n) >> f.s; }
 __device__ __forceinline__ FastDiv fd_of(const unsigned (&v)[3]) { return FastDiv{v[0], v[1], v[2]}; }
+
+// 8-byte asynchronous copy global -> shared (sm_80+), and the wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async8(F* dst_smem, const F* src) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Prefetch into L1: lets a loop with one pending element per thread overlap
 // the L2 latency of later iterations without holding their values in registers.
@@ -556,45 +574,32 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
             for (int j = 0; j < H; ++j) S[j * kZCols] = a[j];
         }
         __syncthreads();
+        // K is even in the z offset for xx, xy, yy, zz and odd for xz, yz, so the spectrum at
+        // frequency -f is +-(the one at f): one load of the six entries serves the z position p of
+        // frequency f and the position pm of -f (mirror pairs; the smaller position does the work)
         const int cst = LZ * kZCols;
-        for (int task = t; task < LZ * nc && task < t + kPf * T; task += T) {
+        constexpr int LGZ = ILog2<LZ>::v;
+        for (int task = t; task < LZ * nc; task += T) {
             const int i = task >> lnc, c = task & (nc - 1);
+            const int f = LGZ ? (int)(__brev((unsigned)i) >> (32 - LGZ)) : 0;
+            const int fm = (LZ - f) & (LZ - 1);
+            const int im = LGZ ? (int)(__brev((unsigned)fm) >> (32 - LGZ)) : 0;
+            if (im < i) continue;
             const F* gp = g.G + i * P + c0 + c;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) pf(gp + q * gc);
-        }
-        for (int task0 = t; task0 < LZ * nc; task0 += kUG * T) {
+            const F gxx = gp[0], gxy = gp[gc], gxz = gp[2 * gc], gyy = gp[3 * gc], gyz = gp[4 * gc], gzz = gp[5 * gc];
             {
-                const int ta = task0 + kPf * T;
-                if (ta < LZ * nc) {
-                    const int i = ta >> lnc, c = ta & (nc - 1);
-                    const F* gp = g.G + i * P + c0 + c;
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) pf(gp + q * gc);
-                }
+                F* q = sm + i * kZCols + c;
+                F X = q[0], Y = q[cst], Z = q[2 * cst];
+                q[0] = cmul(gxx, X) + cmul(gxy, Y) + cmul(gxz, Z);
+                q[cst] = cmul(gxy, X) + cmul(gyy, Y) + cmul(gyz, Z);
+                q[2 * cst] = cmul(gxz, X) + cmul(gyz, Y) + cmul(gzz, Z);
             }
-            F gv[kUG][6];
-#pragma unroll
-            for (int u = 0; u < kUG; ++u) {
-                const int task = task0 + u * T;
-                if (task < LZ * nc) {
-                    const int i = task >> lnc, c = task & (nc - 1);
-                    const F* gp = g.G + i * P + c0 + c;
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) gv[u][q] = gp[q * gc];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kUG; ++u) {
-                const int task = task0 + u * T;
-                if (task < LZ * nc) {
-                    const int i = task >> lnc, c = task & (nc - 1);
-                    F* q = sm + i * kZCols + c;
-                    F X = q[0], Y = q[cst], Z = q[2 * cst];
-                    q[0] = cmul(gv[u][0], X) + cmul(gv[u][1], Y) + cmul(gv[u][2], Z);
-                    q[cst] = cmul(gv[u][1], X) + cmul(gv[u][3], Y) + cmul(gv[u][4], Z);
-                    q[2 * cst] = cmul(gv[u][2], X) + cmul(gv[u][4], Y) + cmul(gv[u][5], Z);
-                }
+            if (im != i) {
+                F* q = sm + im * kZCols + c;
+                F X = q[0], Y = q[cst], Z = q[2 * cst];
+                q[0] = cmul(gxx, X) + cmul(gxy, Y) - cmul(gxz, Z);
+                q[cst] = cmul(gxy, X) + cmul(gyy, Y) - cmul(gyz, Z);
+                q[2 * cst] = cmul(gzz, Z) - cmul(gxz, X) - cmul(gyz, Y);
             }
         }
         __syncthreads();
@@ -635,7 +640,9 @@ __device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, 
     for (int r0 = rk * T; r0 < NR; r0 += nrk * T) {
         const int nr = min(T, NR - r0);
         const F* src = W1 + (int64_t)r0 * LX;
-        for (int k = t; k < nr * LX; k += T) smi[(k / LX) * (LX + 1) + (k & (LX - 1))] = src[k];
+        // asynchronous global -> shared copies (no registers held while in flight), one wait
+        for (int k = t; k < nr * LX; k += T) cp_async8(smi + (k / LX) * (LX + 1) + (k & (LX - 1)), src + k);
+        cp_async_wait_all();
         __syncthreads();
         if (t < nr) {
             const F* row = smi + t * (LX + 1);
@@ -707,7 +714,7 @@ template <class C> struct SmemMvm {
                                   const C* tw, C c1, C c2, double2* red) {
         double2 r = phase_xy<C, IN>(g, voff, W2, chi, sm, tw, c1, c2, red);
         team_sync();
-        return r;
+        return r;                                 // this thread's part of ||s||^2 (IN_S)
     }
     static __device__ void mid(const InnerGroup<C>& g, C* W2, C* sm, const C* tw) {
         phase_z<C>(g, W2, sm, tw);
@@ -715,8 +722,8 @@ template <class C> struct SmemMvm {
     }
     template <int OUT>
     static __device__ void inv(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const uint8_t* mask, C* sm,
-                               const C* tw, double2* red, double2& d1, double2& d2) {
-        phase_xy_inv<C, OUT>(g, voff, W2, mask, sm, tw, red, d1, d2);
+                               const C* tw, double2* red, double2& d1, double2& d2, double extra) {
+        phase_xy_inv<C, OUT>(g, voff, W2, mask, sm, tw, red, d1, d2, extra);
     }
 };
 
@@ -728,10 +735,8 @@ struct RegMvm {
         VIE_LEN_SWITCH(g.lx, (acc = x_fwd_reg<LL, IN>(g, voff, W1, chi, sm, tw, c1, c2)));
         team_sync();
         VIE_LEN_SWITCH(g.ly, (y_fwd_reg<LL>(g, W1, W2, tw)));
-        double2 a = make_double2(acc.x, acc.y), z = make_double2(0, 0);
-        team_sum2(a, z, red);
-        team_sync();          // W2 complete on every rank
-        return a;
+        team_sync();                            // W2 complete on every rank
+        return make_double2(acc.x, acc.y);      // this thread's part of ||s||^2 (IN_S), summed later
     }
     static __device__ __forceinline__ void mid(const InnerGroup<F>& g, F* W2, F* sm, const F* tw) {
         VIE_LEN_SWITCH(g.lz, (z_reg<LL>(g, W2, sm, tw)));
@@ -739,13 +744,13 @@ struct RegMvm {
     }
     template <int OUT>
     static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const uint8_t* mask, F* sm,
-                               const F* tw, double2* red, double2& d1, double2& d2) {
+                               const F* tw, double2* red, double2& d1, double2& d2, double extra) {
         VIE_LEN_SWITCH(g.ly, (y_inv_reg<LL>(g, W2, W1, tw)));
         team_sync();
         F a1 = czero<F>(), a2 = czero<F>();
         VIE_LEN_SWITCH(g.lx, (x_inv_reg<LL, OUT>(g, voff, W1, mask, sm, tw, a1, a2)));
         d1 = make_double2(a1.x, a1.y);
-        d2 = make_double2(a2.x, a2.y);
+        d2 = make_double2(a2.x, extra);          // .y carries a deferred sum (||s||^2)
         team_sum2(d1, d2, red);
     }
 };
@@ -803,27 +808,29 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
         Mvm::mid(g, W, sm, tw);
         if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm);
         double2 sigma, unused;
-        Mvm::template inv<OUT_V>(g, voff, W1, W, mask, sm, tw, red, sigma, unused);
+        Mvm::template inv<OUT_V>(g, voff, W1, W, mask, sm, tw, red, sigma, unused, 0.0);
         if (!dgood(sigma)) { status = SEG_BREAKDOWN; break; }
         alpha = dcdiv(rho, sigma);
-        // s = r - alpha v, and its transform for t = A s
-        double2 sn = Mvm::template fwd<IN_S>(g, voff, W1, W, chi, sm, tw, cmk<C>(alpha.x, alpha.y), czero<C>(), red);
-        if (sn.x <= tol2) {
-            // half-step convergence: x += alpha p
+        // s = r - alpha v and t = A s; ||s||^2 is summed together with <t,s> and <t,t>, so the
+        // half-step test (same value, same decision) costs no reduction of its own
+        double2 snp = Mvm::template fwd<IN_S>(g, voff, W1, W, chi, sm, tw, cmk<C>(alpha.x, alpha.y), czero<C>(), red);
+        Mvm::mid(g, W, sm, tw);
+        if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm + g.kb_upd);
+        double2 ts, tt;
+        Mvm::template inv<OUT_T>(g, voff, W1, W, mask, sm, tw, red, ts, tt, snp.x);
+        const double sn2 = tt.y;
+        if (sn2 <= tol2) {
+            // half-step convergence: x += alpha p (t is not needed)
             C ac = cmk<C>(alpha.x, alpha.y);
             for (int64_t i = (int64_t)rk * blockDim.x + threadIdx.x; i < n; i += (int64_t)nrk * blockDim.x) {
                 int64_t e = voff + i;
                 g.x[e] = g.x[e] + cmul(ac, g.p[e]);
             }
             iters += 0.5;
-            res2 = sn.x;
+            res2 = sn2;
             status = SEG_CONVERGED;
             break;
         }
-        Mvm::mid(g, W, sm, tw);
-        if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm + g.kb_upd);
-        double2 ts, tt;
-        Mvm::template inv<OUT_T>(g, voff, W1, W, mask, sm, tw, red, ts, tt);
         if (!(tt.x > 0.0) || !isfinite(tt.x)) { status = SEG_BREAKDOWN; break; }
         omega = make_double2(ts.x / tt.x, ts.y / tt.x);
         // x += alpha p + omega s, r = s - omega t; rho = <rhat, r>, ||r||^2
@@ -898,6 +905,8 @@ __global__ void __launch_bounds__(kInnerThreads, 2) k_inner(const InnerGroup<C>*
     __shared__ double2 red[2 * (kInnerThreads / 32)];
     __shared__ int item;
     cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x == 0) team_slot = 0;
+    __syncthreads();
     for (;;) {
         // rank 0 of the cluster takes the next block; every rank reads it from rank 0's shared memory
         if (cl.block_rank() == 0 && threadIdx.x == 0) item = atomicAdd(next, 1);
