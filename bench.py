@@ -277,11 +277,8 @@ def main():
         vie.profile_enable(False)
     elapsed = t_all0.elapsed_time(t_all1) / 1e3
     lat = np.array([a.elapsed_time(b) for a, b in ev])
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = args.steps * world / elapsed
+    from paper_2501_13512_gb300 import replicas
+    value, _, elapsed = replicas.aggregate(elapsed, args.steps)   # max time over ranks, sum of solves
     e_mixed = e.clone()
 
     # full-grid MVM throughput in both precisions
