@@ -184,6 +184,8 @@ typedef struct {
     int32_t refinements;     /* MIXED: FP64 residual evaluations after the first    */
     double true_rel_res;     /* ||E_inc - A E|| / ||E_inc||, FP64, at exit          */
     int32_t status;          /* same value as returned                              */
+    int32_t rejected;        /* MIXED: corrections undone because they did not
+                                lower the FP64 residual (vie_solve; batch: 0/1)    */
 } vie_solve_stats;
 
 /* Solves A E = E_inc (Eq. 4) by right-preconditioned BiCGSTAB (Section II.B).
@@ -191,6 +193,9 @@ typedef struct {
  * VIE_MODE_MIXED: FP64 residual r = E_inc - A E (complex128 MVM), then a
  *   complex64 preconditioned BiCGSTAB for A d = r with FP64 reductions and
  *   scalars, E += d, repeated until the FP64 residual meets outer_tol.
+ *   A correction that does not lower the FP64 residual is undone; the next
+ *   one is then solved without the preconditioner, and if that one fails too
+ *   the solve stops with VIE_ENOTCONV and the best E so far.
  * einc_dev, e_dev: complex128 vectors (caller-owned, distinct). The spectrum
  * must hold VIE_C128, and VIE_C64 too for MIXED. Returns VIE_OK,
  * VIE_ENOTCONV (E and stats still valid), VIE_EBREAKDOWN, VIE_ETIMEOUT,
@@ -227,7 +232,8 @@ int vie_batch_destroy(vie_batch* batch);
  * one persistent launch (one CTA cluster per instance) when the padded plane
  * fits in shared memory, else batched launches per BiCGSTAB step; E += d.
  * outer_maxit bounds each correction; inner_tol, inner_maxit and use_precond
- * are ignored (no blocks). einc_dev, e_dev: DEVICE complex128
+ * are ignored (no blocks). An instance whose correction does not lower its
+ * FP64 residual gets that correction undone and stops (VIE_ENOTCONV). einc_dev, e_dev: DEVICE complex128
  * [count][3][nz][ny][nx], distinct. stats: NULL or count entries
  * (outer_iters = correction iterations summed over refinements).
  * Returns VIE_OK when every instance meets outer_tol, VIE_ENOTCONV otherwise

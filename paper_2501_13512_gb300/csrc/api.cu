@@ -789,6 +789,7 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
     double bn2 = 0;
     VIE_TRY(read_scalar(g, g->dscal, &bn2, s, tmo));
     int rc = VIE_OK;
+    bool stalled = false;                  // MIXED stopped on a correction that did not help
     if (o->mode == VIE_MODE_PLAIN_C128) {
         KrylovVecs<double2> v = g->o128;
         v.b = const_cast<double2*>(b);
@@ -799,29 +800,51 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
         rc = status_code(fs.status);
         VIE_TRY(true_residual(g, sp, b, x, g->o128.r, bn2, &st.true_rel_res, s, tmo, acc));
     } else {
-        // iterative refinement: FP64 residual, complex64 preconditioned correction
+        // iterative refinement: FP64 residual, complex64 preconditioned correction. A correction is
+        // kept only if it lowers the FP64 residual. Otherwise it is undone and, once, the correction
+        // is solved again without the preconditioner: when inner block solves stall (blocks of a
+        // metal with Re(eps_r) < 0 at a loose inner tolerance), the inexact preconditioner changes
+        // from one application to the next and the preconditioned iteration can diverge.
         const int maxref = o->max_refinements > 0 ? o->max_refinements : 8;
         VIE_CK(cudaMemsetAsync(x, 0, n3 * sizeof(double2), s));
         VIE_TRY(vec_copy<double2>(b, g->o128.r, n3, s));
         double rel = bn2 > 0 ? 1.0 : 0.0;
-        double rn2 = bn2;
+        double prev = rel;
         VIE_CK(cudaMemcpyAsync(g->dscal + 1, g->dscal, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        vie_solve_opts oc = *o;            // options of the correction solves
         rc = VIE_ENOTCONV;
         for (int ref = 0; ref <= maxref; ++ref) {
             if (ref > 0) {
                 VIE_TRY(true_residual(g, sp, b, x, g->o128.r, bn2, &rel, s, tmo, acc));
                 st.refinements++;
+                if (!(rel < prev)) {       // also catches a non-finite residual: restore E and r
+                    VIE_TRY(vec_copy<double2>(g->o128.p, x, n3, s));
+                    VIE_TRY(vec_copy<double2>(g->o128.s, g->o128.r, n3, s));
+                    VIE_CK(cudaMemcpyAsync(g->dscal + 1, g->dscal + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+                    st.rejected++;
+                    rel = prev;
+                    if (!oc.use_precond || g->nblocks == 0) {
+                        stalled = true;
+                        break;
+                    }
+                    oc.use_precond = 0;
+                }
             }
             if (rel <= o->outer_tol) {
                 rc = VIE_OK;
                 break;
             }
             if (ref == maxref) break;
-            (void)rn2;
+            prev = rel;
+            // E, r and ||r||^2 before this correction, kept for undoing it (p and s of the
+            // complex128 Krylov set are free in this mode)
+            VIE_TRY(vec_copy<double2>(x, g->o128.p, n3, s));
+            VIE_TRY(vec_copy<double2>(g->o128.r, g->o128.s, n3, s));
+            VIE_CK(cudaMemcpyAsync(g->dscal + 2, g->dscal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
             VIE_TRY(vec_scale_to_c64(g->o128.r, g->dscal + 1, g->o64.b, n3, s));
             const double eta = std::max(0.5 * o->outer_tol / rel, 1e-4);
             SegState fs;
-            VIE_TRY(bicgstab_full<float2>(g, sp, g->o64, o, std::min(eta, 0.5), o->outer_maxit, s, acc, &fs));
+            VIE_TRY(bicgstab_full<float2>(g, sp, g->o64, &oc, std::min(eta, 0.5), o->outer_maxit, s, acc, &fs));
             st.outer_iters += fs.iters;
             if (fs.status == SEG_BREAKDOWN && fs.iters == 0) {
                 rc = VIE_EBREAKDOWN;
@@ -838,7 +861,9 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
     st.status = rc;
     if (stats) *stats = st;
     if (rc != VIE_OK) {
-        if (rc == VIE_ENOTCONV) set_error("vie_solve: iteration limit reached before the tolerance");
+        if (rc == VIE_ENOTCONV)
+            set_error(stalled ? "vie_solve: a correction did not lower the FP64 residual (undone); stopped"
+                                  : "vie_solve: iteration limit reached before the tolerance");
         if (rc == VIE_EBREAKDOWN) set_error("vie_solve: BiCGSTAB breakdown");
     }
     return rc;

@@ -27,6 +27,7 @@ struct vie_batch {
     vie::ReduceScratch red;
     double2* r128 = nullptr;              // FP64 residuals
     double2* tmp128 = nullptr;            // A x
+    double2* xprev = nullptr;             // E before the last correction
     double* d_bn2 = nullptr;              // [count] ||E_inc||^2
     double* d_rn2 = nullptr;              // [count] ||r||^2
     double* d_tols = nullptr;             // [count] correction tolerances (0: instance done)
@@ -120,6 +121,13 @@ __global__ void k_seg_add(double2* x, const float2* d, const double* rn2, const 
     }
 }
 
+// x = xprev for instances whose last correction is undone (sel > 0).
+__global__ void k_seg_restore(double2* x, const double2* xprev, const double* sel, int64_t seglen, int count) {
+    const int64_t n = seglen * count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (sel[i / seglen] > 0.0) x[i] = xprev[i];
+}
+
 __global__ void k_fill_u8(uint8_t* p, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = 1;
@@ -185,7 +193,7 @@ extern "C" int vie_batch_create(const vie_batch_desc* d, vie_batch** out) {
     if ((rc = balloc(b, &k.b, nv)) || (rc = balloc(b, &k.x, nv)) || (rc = balloc(b, &k.r, nv)) ||
         (rc = balloc(b, &k.rhat, nv)) || (rc = balloc(b, &k.p, nv)) || (rc = balloc(b, &k.v, nv)) ||
         (rc = balloc(b, &k.s, nv)) || (rc = balloc(b, &k.t, nv)) || (rc = balloc(b, &b->r128, nv)) ||
-        (rc = balloc(b, &b->tmp128, nv)) || (rc = balloc(b, &b->st, d->count)) ||
+        (rc = balloc(b, &b->tmp128, nv)) || (rc = balloc(b, &b->xprev, nv)) || (rc = balloc(b, &b->st, d->count)) ||
         (rc = balloc(b, &b->d_bn2, d->count)) || (rc = balloc(b, &b->d_rn2, d->count)) ||
         (rc = balloc(b, &b->d_tols, d->count)) || (rc = balloc(b, &b->d_gb128, d->count)) ||
         (rc = balloc(b, &b->d_gb64, d->count)))
@@ -290,7 +298,8 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
     VIE_CK(cudaMemcpyAsync(b->d_rn2, b->d_bn2, nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
     rn2 = bn2;
     const int maxref = o->max_refinements > 0 ? o->max_refinements : 8;
-    std::vector<double> tols(nb);
+    std::vector<double> tols(nb, 0.0), undo(nb, 0.0), prev(nb, 1.0);
+    std::vector<char> stopped(nb, 0);
     int mv128 = 0;
     for (int ref = 0; ref <= maxref; ++ref) {
         if (ref > 0) {
@@ -304,10 +313,28 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
             VIE_TRY(wait_ev(b->ev, tmo));
             for (int i = 0; i < nb; ++i) rn2[i] = b->h_scal[i];
         }
-        int active = 0;
+        // an instance whose correction did not lower its FP64 residual gets it undone and stops
+        int nundo = 0;
         for (int i = 0; i < nb; ++i) {
             rel[i] = bn2[i] > 0 ? std::sqrt(rn2[i] / bn2[i]) : 0.0;
-            if (rel[i] <= o->outer_tol) {
+            undo[i] = 0.0;
+            if (ref > 0 && tols[i] > 0.0 && !(rel[i] < prev[i])) {
+                undo[i] = 1.0;
+                ++nundo;
+                stopped[i] = 1;
+                rel[i] = prev[i];
+            }
+        }
+        if (nundo) {
+            VIE_CK(cudaMemcpyAsync(b->d_tols, undo.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
+            k_seg_restore<<<grid1(nv), 256, 0, s>>>(x, b->xprev, b->d_tols, b->n3, nb);
+            VIE_CK(cudaGetLastError());
+        }
+        int active = 0;
+        for (int i = 0; i < nb; ++i) {
+            if (stopped[i]) {
+                tols[i] = 0.0;
+            } else if (rel[i] <= o->outer_tol) {
                 if (status[i] != VIE_OK) refs[i] = ref;
                 status[i] = VIE_OK;
                 tols[i] = 0.0;
@@ -315,8 +342,10 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
                 tols[i] = std::min(0.5, std::max(0.5 * o->outer_tol / rel[i], 1e-4));
                 ++active;
             }
+            prev[i] = rel[i];
         }
         if (active == 0 || ref == maxref) break;
+        VIE_TRY(vec_copy<double2>(x, b->xprev, nv, s));
         VIE_CK(cudaMemcpyAsync(b->d_tols, tols.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
         k_seg_scale<<<grid1(nv), 256, 0, s>>>(b->r128, b->d_rn2, b->d_tols, b->k64.b, b->n3, nb);
         VIE_CK(cudaGetLastError());
@@ -374,6 +403,7 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
             stats[i].true_rel_res = rel[i];
             stats[i].status = status[i];
             stats[i].refinements = refs[i];
+            stats[i].rejected = stopped[i];
             stats[i].matvecs_c128 = mv128;
         }
     }

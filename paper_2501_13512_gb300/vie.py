@@ -56,7 +56,7 @@ class SolveOpts(ctypes.Structure):
 class SolveStats(ctypes.Structure):
     _fields_ = [("outer_iters", c_double), ("inner_iters", c_int64), ("precond_applies", c_int32),
                 ("matvecs_c128", c_int32), ("matvecs_c64", c_int32), ("refinements", c_int32),
-                ("true_rel_res", c_double), ("status", c_int32)]
+                ("true_rel_res", c_double), ("status", c_int32), ("rejected", c_int32)]
 
 
 class BatchDesc(ctypes.Structure):
