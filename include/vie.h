@@ -172,6 +172,9 @@ typedef struct {
     int32_t mode;            /* vie_solve_mode                                      */
     int32_t max_refinements; /* MIXED: FP64 residual corrections, 0 = default (8)   */
     double wait_timeout_ms;  /* bound on each host wait for the device, 0 = 60000   */
+    const void* x0_dev;      /* initial guess E_0 (DEVICE complex128, the layout of
+                                E), or NULL for E_0 = 0; may be e_dev itself (warm
+                                start in place); must be NULL for vie_batch_solve  */
 } vie_solve_opts;
 
 typedef struct {
@@ -186,6 +189,8 @@ typedef struct {
     int32_t status;          /* same value as returned                              */
     int32_t rejected;        /* MIXED: corrections undone because they did not
                                 lower the FP64 residual (vie_solve; batch: 0/1)    */
+    double elapsed_ms;       /* host wall time of the call (batch: of the whole
+                                batch, the same in every entry)                    */
 } vie_solve_stats;
 
 /* Solves A E = E_inc (Eq. 4) by right-preconditioned BiCGSTAB (Section II.B).

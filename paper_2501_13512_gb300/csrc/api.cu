@@ -777,6 +777,10 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
         return fail(VIE_EINVAL, "vie_solve: bad inner tolerance or maxit");
     const int64_t n3 = 3 * g->N;
     if (overlaps(einc, e, n3 * 16)) return fail(VIE_EINVAL, "vie_solve: einc and e overlap");
+    const double2* x0 = (const double2*)o->x0_dev;
+    if (x0 && x0 != (const double2*)e && (overlaps(x0, e, n3 * 16) || overlaps(x0, einc, n3 * 16)))
+        return fail(VIE_EINVAL, "vie_solve: x0 overlaps einc, or overlaps e without being e");
+    const auto t_start = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     const double tmo = o->wait_timeout_ms;
     SolveAccum acc;
@@ -788,16 +792,31 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
     VIE_TRY(vec_norm2_128(b, n3, &g->ored, g->dscal, s));
     double bn2 = 0;
     VIE_TRY(read_scalar(g, g->dscal, &bn2, s, tmo));
+    if (!(bn2 > 0.0)) x0 = nullptr;        // E_inc = 0: the solution is 0 whatever the guess
     int rc = VIE_OK;
     bool stalled = false;                  // MIXED stopped on a correction that did not help
     if (o->mode == VIE_MODE_PLAIN_C128) {
         KrylovVecs<double2> v = g->o128;
         v.b = const_cast<double2*>(b);
         v.x = x;
+        double tol = o->outer_tol;
+        if (x0) {
+            // BiCGSTAB from E_0 is BiCGSTAB from 0 on A d = r_0 = E_inc - A E_0, E = E_0 + d,
+            // with the stopping test still relative to ||E_inc||
+            double rel0 = 0;
+            VIE_TRY(true_residual(g, sp, b, x0, g->tmp128, bn2, &rel0, s, tmo, acc));
+            v.b = g->tmp128;
+            if (x0 == (const double2*)x) {
+                if (!g->x0buf) VIE_TRY(dalloc(g, &g->x0buf, n3));
+                v.x = g->x0buf;
+            }
+            tol = rel0 > 0 ? o->outer_tol / rel0 : o->outer_tol;
+        }
         SegState fs;
-        VIE_TRY(bicgstab_full<double2>(g, sp, v, o, o->outer_tol, o->outer_maxit, s, acc, &fs));
+        VIE_TRY(bicgstab_full<double2>(g, sp, v, o, tol, o->outer_maxit, s, acc, &fs));
         st.outer_iters = fs.iters;
         rc = status_code(fs.status);
+        if (x0) VIE_TRY(vec_sum128(x0, v.x, x, n3, s));
         VIE_TRY(true_residual(g, sp, b, x, g->o128.r, bn2, &st.true_rel_res, s, tmo, acc));
     } else {
         // iterative refinement: FP64 residual, complex64 preconditioned correction. A correction is
@@ -806,11 +825,16 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
         // metal with Re(eps_r) < 0 at a loose inner tolerance), the inexact preconditioner changes
         // from one application to the next and the preconditioned iteration can diverge.
         const int maxref = o->max_refinements > 0 ? o->max_refinements : 8;
-        VIE_CK(cudaMemsetAsync(x, 0, n3 * sizeof(double2), s));
-        VIE_TRY(vec_copy<double2>(b, g->o128.r, n3, s));
         double rel = bn2 > 0 ? 1.0 : 0.0;
+        if (x0) {
+            if (x0 != (const double2*)x) VIE_TRY(vec_copy<double2>(x0, x, n3, s));
+            VIE_TRY(true_residual(g, sp, b, x, g->o128.r, bn2, &rel, s, tmo, acc));
+        } else {
+            VIE_CK(cudaMemsetAsync(x, 0, n3 * sizeof(double2), s));
+            VIE_TRY(vec_copy<double2>(b, g->o128.r, n3, s));
+            VIE_CK(cudaMemcpyAsync(g->dscal + 1, g->dscal, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
         double prev = rel;
-        VIE_CK(cudaMemcpyAsync(g->dscal + 1, g->dscal, sizeof(double), cudaMemcpyDeviceToDevice, s));
         vie_solve_opts oc = *o;            // options of the correction solves
         rc = VIE_ENOTCONV;
         for (int ref = 0; ref <= maxref; ++ref) {
@@ -859,6 +883,7 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
     st.matvecs_c128 = acc.mv128;
     st.matvecs_c64 = acc.mv64;
     st.status = rc;
+    st.elapsed_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = st;
     if (rc != VIE_OK) {
         if (rc == VIE_ENOTCONV)

@@ -246,6 +246,8 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
                                const vie_solve_opts* o, vie_stream_t stream, vie_solve_stats* stats) {
     if (!b || !k0s || !einc_dev || !e_dev || !o) return fail(VIE_EINVAL, "vie_batch_solve: null argument");
     if (o->mode != VIE_MODE_MIXED) return fail(VIE_EINVAL, "vie_batch_solve: only VIE_MODE_MIXED is supported");
+    if (o->x0_dev) return fail(VIE_EINVAL, "vie_batch_solve: x0_dev must be NULL");
+    const auto t_start = std::chrono::steady_clock::now();
     if (!(o->outer_tol > 0.0) || o->outer_maxit < 1) return fail(VIE_EINVAL, "vie_batch_solve: bad tolerance or maxit");
     const int nb = b->count;
     const int64_t nv = b->n3 * nb;
@@ -404,6 +406,8 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
             stats[i].status = status[i];
             stats[i].refinements = refs[i];
             stats[i].rejected = stopped[i];
+            stats[i].elapsed_ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
             stats[i].matvecs_c128 = mv128;
         }
     }

@@ -98,11 +98,13 @@ __device__ void finalize(SegState& s, double2 d1, double2 d2, int* n_active, dou
         s.rho = s.rho_prev = s.alpha = s.omega = make_double2(1.0, 0.0);
         s.iters = 0.0;
         s.maxit = maxit;
-        if (d1.x > 0.0 && isfinite(d1.x)) {
+        if (!isfinite(d1.x)) {
+            s.status = SEG_BREAKDOWN;
+        } else if (d1.x == 0.0 || d1.x <= s.tol2) {   // x0 already meets the tolerance (tol >= 1)
+            s.status = SEG_CONVERGED;
+        } else {
             s.status = SEG_ACTIVE;
             atomicAdd(n_active, 1);
-        } else {
-            s.status = d1.x == 0.0 ? SEG_CONVERGED : SEG_BREAKDOWN;
         }
     } else if (OP == OP_RHO) {
         s.rho = d1;
@@ -349,6 +351,18 @@ int vec_norm2_128(const double2* a, int64_t n, ReduceScratch* red, double* d_out
     int nct = (int)std::max<int64_t>(1, std::min<int64_t>(want, kMaxCtaPerSeg));
     prof_begin(s, PK_FIELD, VIE_C128, 0, n * 16, false);
     k_norm2<<<nct, kRedThreads, 0, s>>>(a, n, red->part, red->count, d_out);
+    prof_end(s);
+    VIE_CK(cudaGetLastError());
+    return VIE_OK;
+}
+
+__global__ void k_sum128(const double2* a, const double2* b, double2* out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] + b[i];
+}
+int vec_sum128(const double2* a, const double2* b, double2* out, int64_t n, cudaStream_t s) {
+    prof_begin(s, PK_FIELD, VIE_C128, 0, 3 * n * 16, false);
+    k_sum128<<<grid_for(n), 256, 0, s>>>(a, b, out, n);
     prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;

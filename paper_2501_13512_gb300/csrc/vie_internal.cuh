@@ -163,6 +163,7 @@ struct vie_grid {
     vie::KrylovVecs<double2> o128;
     vie::KrylovVecs<float2> o64;
     double2* tmp128 = nullptr;            // full-grid scratch vector
+    double2* x0buf = nullptr;             // plain solves warm-started in place (allocated on first use)
     float2* tmp64 = nullptr;
     vie::SegState* ost = nullptr;         // outer state [1]
     vie::ReduceScratch ored;
@@ -241,6 +242,7 @@ int reduce_count_active(const SegState* st, int nseg, int* n_active, cudaStream_
 template <class C> int vec_copy(const C* a, C* b, int64_t n, cudaStream_t s);
 int vec_residual128(const double2* b, const double2* ax, double2* r, int64_t n, cudaStream_t s);
 int vec_norm2_128(const double2* a, int64_t n, ReduceScratch* red, double* d_out, cudaStream_t s);
+int vec_sum128(const double2* a, const double2* b, double2* out, int64_t n, cudaStream_t s);   // out = a + b
 int vec_scale_to_c64(const double2* a, const double* d_norm2, float2* b, int64_t n, cudaStream_t s);
 int vec_add_scaled_c64(double2* x, const float2* d, const double* d_norm2, int64_t n, cudaStream_t s);
 

@@ -50,13 +50,14 @@ class PrecondStats(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("outer_tol", c_double), ("inner_tol", c_double), ("outer_maxit", c_int32),
                 ("inner_maxit", c_int32), ("use_precond", c_int32), ("mode", c_int32),
-                ("max_refinements", c_int32), ("wait_timeout_ms", c_double)]
+                ("max_refinements", c_int32), ("wait_timeout_ms", c_double), ("x0", c_void_p)]
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("outer_iters", c_double), ("inner_iters", c_int64), ("precond_applies", c_int32),
                 ("matvecs_c128", c_int32), ("matvecs_c64", c_int32), ("refinements", c_int32),
-                ("true_rel_res", c_double), ("status", c_int32), ("rejected", c_int32)]
+                ("true_rel_res", c_double), ("status", c_int32), ("rejected", c_int32),
+                ("elapsed_ms", c_double)]
 
 
 class BatchDesc(ctypes.Structure):
@@ -271,10 +272,12 @@ class Grid:
         return y, _struct_dict(st)
 
     def solve(self, spec, einc, e=None, outer_tol=1e-6, inner_tol=1e-2, outer_maxit=1000, inner_maxit=100,
-              use_precond=True, mode=MODE_MIXED, max_refinements=0, wait_timeout_ms=0.0, check=True):
+              use_precond=True, mode=MODE_MIXED, max_refinements=0, wait_timeout_ms=0.0, x0=None, check=True):
+        """x0: initial guess (complex128 CUDA tensor, may be `e` itself), None for zero."""
         e = self.empty(C128) if e is None else e
         o = SolveOpts(float(outer_tol), float(inner_tol), int(outer_maxit), int(inner_maxit), int(bool(use_precond)),
-                      int(mode), int(max_refinements), float(wait_timeout_ms))
+                      int(mode), int(max_refinements), float(wait_timeout_ms),
+                      None if x0 is None else self._vec(x0, C128, "x0"))
         st = SolveStats()
         rc = load().vie_solve(self.handle, spec.handle, self._vec(einc, C128, "einc"), self._vec(e, C128, "e"),
                               byref(o), _stream(), byref(st))

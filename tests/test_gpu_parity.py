@@ -231,3 +231,38 @@ def test_solve_zero_rhs():
         e, st = g.solve(sp, z, mode=mode)
         assert st["status"] == vie.VIE_OK
         assert not np.any(host(e))
+
+
+@pytest.mark.parametrize("mode", [vie.MODE_PLAIN_C128, vie.MODE_MIXED])
+def test_solve_warm_start(mode):
+    # E_0 = the converged field: no iteration; E_0 = a partial solve (in place): finishes to tolerance
+    w = inputs.metasurface(cells=2, seed=4)
+    ein = osolve.plane_wave(w.n, w.h, w.k0, w.khat, w.pol)
+    A = omvm.FFTOperator(w.eps_r, w.h, w.k0)
+    g = vie.Grid.from_workload(w)
+    sp = g.spectrum(w.k0)
+    b = dev(ein)
+    e_ref, st = g.solve(sp, b, outer_tol=1e-8, mode=vie.MODE_PLAIN_C128)
+    assert st["status"] == vie.VIE_OK and st["elapsed_ms"] > 0
+    e, st = g.solve(sp, b, outer_tol=1e-6, mode=mode, x0=e_ref)
+    assert st["status"] == vie.VIE_OK and st["outer_iters"] == 0
+    assert rel(host(e), host(e_ref)) <= 1e-12
+    e, st0 = g.solve(sp, b, outer_tol=1e-6, mode=mode, outer_maxit=3, max_refinements=1)
+    assert st0["status"] == vie.VIE_ENOTCONV
+    e, st = g.solve(sp, b, e=e, outer_tol=1e-6, mode=mode, x0=e)
+    assert st["status"] == vie.VIE_OK
+    eh = host(e)
+    r = np.linalg.norm(ein - A(eh)) / np.linalg.norm(ein)
+    assert r <= 1.05e-6 and abs(r - st["true_rel_res"]) <= 1e-3 * r
+
+
+def test_solve_rejects_overlapping_x0():
+    eps_r, bid, x = inputs.random_case((6, 5, 4), seed=3, block_grid=(3, 3, 2))
+    g = vie.Grid(eps_r, H, bid)
+    sp = g.spectrum(K0)
+    buf = torch.zeros((2,) + (3, 4, 5, 6), dtype=torch.complex128, device="cuda")
+    b, e = dev(x), buf[0]
+    lib = vie.load()
+    o = vie.SolveOpts(1e-6, 1e-2, 10, 10, 1, vie.MODE_MIXED, 0, 0.0, b.data_ptr())
+    st = vie.SolveStats()
+    assert lib.vie_solve(g.handle, sp.handle, b.data_ptr(), e.data_ptr(), o, None, st) == vie.VIE_EINVAL
