@@ -50,7 +50,7 @@ class PrecondStats(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("outer_tol", c_double), ("inner_tol", c_double), ("outer_maxit", c_int32),
                 ("inner_maxit", c_int32), ("use_precond", c_int32), ("mode", c_int32),
-                ("max_refinements", c_int32), ("wait_timeout_ms", c_double), ("x0", c_void_p)]
+                ("max_refinements", c_int32), ("wait_timeout_ms", c_double), ("x0_dev", c_void_p)]
 
 
 class SolveStats(ctypes.Structure):

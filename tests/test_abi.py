@@ -2,6 +2,7 @@
 import ctypes
 import os
 import re
+import subprocess
 
 from paper_2501_13512_gb300 import build, vie
 
@@ -32,8 +33,28 @@ def test_error_text_roundtrip_without_gpu():
     assert "null" in vie.last_error()
 
 
-def test_struct_sizes_match_header_layout():
-    # field order and widths of the public structs, as laid out by the C compiler
-    assert ctypes.sizeof(vie.GridDesc) == 4 * 3 + 4 + 8 + 8 + 8 + 8
-    assert ctypes.sizeof(vie.SolveOpts) == 8 + 8 + 4 * 5 + 4 + 8
-    assert ctypes.sizeof(vie.PrecondStats) == 4 + 4 + 8 + 4 + 4
+STRUCTS = {"vie_grid_desc": "GridDesc", "vie_grid_info": "GridInfo", "vie_precond_stats": "PrecondStats",
+           "vie_solve_opts": "SolveOpts", "vie_solve_stats": "SolveStats", "vie_batch_desc": "BatchDesc",
+           "vie_kernel_stat": "KernelStat"}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # every field offset and struct size of the ctypes binding, against the C compiler's layout of include/vie.h
+    lines = ["#include <stddef.h>", "#include <stdio.h>", f'#include "{vie.HEADER}"', "int main(void) {"]
+    for cname, pyname in STRUCTS.items():
+        cls = getattr(vie, pyname)
+        lines.append(f'printf("{pyname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{pyname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    for pyname in STRUCTS.values():
+        cls = getattr(vie, pyname)
+        assert got[(pyname, "size")] == ctypes.sizeof(cls), pyname
+        for field, _ in cls._fields_:
+            assert got[(pyname, field)] == getattr(cls, field).offset, (pyname, field)
