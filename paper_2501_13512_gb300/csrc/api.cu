@@ -222,6 +222,7 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
     }
     g->full.nb = 1;
     set_shape(g->full, d->nx, d->ny, d->nz);
+    g->full.oct = true;                   // the full-grid spectrum is stored octant-compressed
     int rc = upload_chi(g, g->full, chi);
     if (rc) return bail(rc);
     if ((rc = alloc_fft_work(g, g->full))) return bail(rc);
@@ -417,6 +418,23 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
     std::vector<const BoxSet*> sets;
     sets.push_back(&g->full);
     for (auto& gr : g->groups) sets.push_back(&gr.bs);
+    {
+        // full grid: octant-compressed spectra, built from an FP64 temporary
+        const int64_t n = 6 * g->full.oct_elems();
+        double2* G = nullptr;
+        float2* G64 = nullptr;
+        if (((mask & VIE_C128) && cudaMalloc(&G, n * sizeof(double2)) != cudaSuccess) ||
+            ((mask & VIE_C64) && cudaMalloc(&G64, n * sizeof(float2)) != cudaSuccess)) {
+            cudaGetLastError();
+            if (G) cudaFree(G);
+            return bail(fail(VIE_ENOMEM, "spectrum allocation failed"));
+        }
+        sp->g128.push_back(G);
+        sp->g64.push_back(G64);
+        int rc = spectrum_build(g->full, k0, g->h, G, G64, nullptr, s);
+        if (rc) return bail(rc);
+    }
+    sets.erase(sets.begin());
     for (const BoxSet* bs : sets) {
         const int64_t n = 6 * bs->spec_elems();
         double2* G = nullptr;
@@ -445,7 +463,7 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
         // the FP64 spectrum was only the source of the complex64 copy
         if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(VIE_ECUDA, "spectrum generation failed"));
         for (auto& p : sp->g128) {
-            cudaFree(p);
+            if (p) cudaFree(p);
             p = nullptr;
         }
     }

@@ -168,6 +168,7 @@ extern "C" int vie_batch_create(const vie_batch_desc* d, vie_batch** out) {
     b->n3 = 3 * N;
     BoxSet& bs = b->bs;
     bs.nb = d->count;
+    bs.oct = true;      // complex128 spectra (and complex64 ones outside the persistent solver) are octant-compressed
     bs.bx = d->nx; bs.by = d->ny; bs.bz = d->nz;
     bs.Mx = p2(2 * d->nx - 1); bs.My = p2(2 * d->ny - 1); bs.Mz = p2(2 * d->nz - 1);
     bs.lx = lg2i(bs.Mx); bs.ly = lg2i(bs.My); bs.lz = lg2i(bs.Mz);
@@ -262,22 +263,30 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
     // spectra per distinct wavenumber (cached), one pointer per instance
     std::vector<double2*> gb128(nb);
     std::vector<float2*> gb64(nb);
-    const int64_t sv = 6 * bs.spec_elems();
+    // complex128: octant layout (batched MVMs); complex64: full layout when the persistent
+    // block solver reads it, else octant layout
+    const int64_t so = 6 * bs.oct_elems();
+    const int64_t s64 = b->persistent ? 6 * bs.spec_elems() : so;
     for (int i = 0; i < nb; ++i) {
         auto it = b->spectra.find(k0s[i]);
         if (it == b->spectra.end()) {
             double2* G = nullptr;
             float2* G64 = nullptr;
-            if (cudaMalloc(&G, sv * sizeof(double2)) != cudaSuccess || cudaMalloc(&G64, sv * sizeof(float2)) != cudaSuccess) {
+            if (cudaMalloc(&G, so * sizeof(double2)) != cudaSuccess || cudaMalloc(&G64, s64 * sizeof(float2)) != cudaSuccess) {
                 cudaGetLastError();
                 if (G) cudaFree(G);
                 return fail(VIE_ENOMEM, "vie_batch_solve: spectrum allocation failed");
             }
             BoxSet one = bs;
             one.nb = 1;
-            VIE_TRY(green_sample(one, k0s[i], b->h, G, s));
-            VIE_TRY(spectrum_fft<double2>(one, G, s));
-            VIE_TRY(convert_c128_to_c64(G, G64, sv, s));
+            int rc = spectrum_build(one, k0s[i], b->h, G, b->persistent ? nullptr : G64,
+                                    b->persistent ? G64 : nullptr, s);
+            if (rc) {
+                cudaStreamSynchronize(s);
+                cudaFree(G);
+                cudaFree(G64);
+                return rc;
+            }
             it = b->spectra.emplace(k0s[i], std::make_pair(G, G64)).first;
         }
         gb128[i] = it->second.first;

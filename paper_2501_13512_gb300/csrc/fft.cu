@@ -17,6 +17,8 @@
 //   pass X' inverse, keep x < bx, y = x - u (masked)         -> y
 // Each pass stages a tile of pencils in shared memory; global accesses are
 // along the contiguous x axis in every pass.
+#include <algorithm>
+
 #include "fft_core.cuh"
 #include "vie_internal.cuh"
 
@@ -149,11 +151,12 @@ __global__ void __launch_bounds__(kThreads) k_cols(ColArgs<C> a) {
 // ---------------------------------------------------------------- pass Z fused with the Green multiply
 template <class C> struct ZArgs {
     C* w;                 // w2 of the BoxSet
-    const C* G;           // [6][Mz][My][Mx]
+    const C* G;           // [6][Mz][My][Mx], or [6][Mz/2+1][My/2+1][Mx/2+1] when oct
     const C* const* Gb;   // optional: one spectrum per box (instances with their own wavenumber)
     const SegState* st;
     const C* tw;
     int ncols, nzb, lL, ltc, twshift;
+    int oct, lx, ly;      // octant-compressed spectrum; log2 Mx, log2 My
     int64_t axis, comp_stride, box_stride, gcomp;
     int* units;
 };
@@ -184,9 +187,22 @@ __global__ void __launch_bounds__(kThreads) k_zgreen(ZArgs<C> a) {
     for (int idx = threadIdx.x; idx < L * TC; idx += blockDim.x) {
         int c = idx & (TC - 1), i = idx >> a.ltc;
         if (c >= ncol) continue;
-        const C* g = (a.Gb ? a.Gb[b] : a.G) + i * a.axis + col0 + c;
+        const C* g = a.Gb ? a.Gb[b] : a.G;
+        bool ux = false, uy = false, uz = false;
+        if (a.oct) {
+            const int col = col0 + c;
+            const int qx = octant_slot(col & ((1 << a.lx) - 1), a.lx, ux);
+            const int qy = octant_slot(col >> a.lx, a.ly, uy);
+            const int qz = octant_slot(i, a.lL, uz);
+            g += ((int64_t)qz * ((1 << a.ly) / 2 + 1) + qy) * ((1 << a.lx) / 2 + 1) + qx;
+        } else {
+            g += i * a.axis + col0 + c;
+        }
         C gxx = g[0], gxy = g[a.gcomp], gxz = g[2 * a.gcomp];
         C gyy = g[3 * a.gcomp], gyz = g[4 * a.gcomp], gzz = g[5 * a.gcomp];
+        if (ux != uy) gxy = mk(-gxy.x, -gxy.y);
+        if (ux != uz) gxz = mk(-gxz.x, -gxz.y);
+        if (uy != uz) gyz = mk(-gyz.x, -gyz.y);
         C* p = buf + i * pitch + c;
         C X = p[0], Y = p[TC], Z = p[2 * TC];
         p[0] = cmul(gxx, X) + cmul(gxy, Y) + cmul(gxz, Z);
@@ -304,7 +320,7 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     const int64_t bv = 3LL * box * es;                            // x or y per box
     const Prof px{PK_X_FWD, bv + box * es + b1, 0};
     const Prof py{PK_Y_FWD, b1 + b2, 0};
-    const Prof pz{PK_Z_GREEN, 2 * b2, 6LL * bs.Mz * planeXY * es};
+    const Prof pz{PK_Z_GREEN, 2 * b2, 6LL * (bs.oct ? bs.oct_elems() : bs.spec_elems()) * es};
     const Prof piy{PK_Y_INV, b2 + b1, 0};
     const Prof pix{PK_X_INV, b1 + 2 * bv + (bs.mask ? box : 0), 0};
 
@@ -332,7 +348,8 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     z.w = w2; z.G = G; z.Gb = Gb; z.st = st; z.tw = T;
     z.ncols = (int)planeXY; z.nzb = bs.bz; z.lL = bs.lz; z.twshift = kLogLmax - bs.lz;
     z.axis = planeXY; z.comp_stride = (int64_t)bs.bz * planeXY; z.box_stride = 3 * z.comp_stride;
-    z.gcomp = (int64_t)bs.Mz * planeXY;
+    z.gcomp = bs.oct ? bs.oct_elems() : (int64_t)bs.Mz * planeXY;
+    z.oct = bs.oct ? 1 : 0; z.lx = bs.lx; z.ly = bs.ly;
     VIE_TRY(launch_zgreen<C>(z, bs.nb, pz, s));
 
     // pass Y inverse: keep y < by
@@ -384,6 +401,55 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* twp) {
     cz.in_s2 = cz.out_s2 = vol;
     VIE_TRY((launch_cols<C, true>(cz, 1, 6, Prof{PK_SPECTRUM, 2 * vol * es, 0}, s)));
     return VIE_OK;
+}
+
+// Octant compression (layout in vie_internal.cuh): slot (c, qz, qy, qx) takes the
+// entry at the positions of the folded frequencies, converted to C.
+template <class C>
+__global__ void k_octant_compress(const double2* full, C* oct, int lx, int ly, int lz) {
+    const int hx = (1 << lx) / 2 + 1, hy = (1 << ly) / 2 + 1, hz = (1 << lz) / 2 + 1;
+    const int64_t per = (int64_t)hx * hy * hz;
+    const int64_t vol = (int64_t)1 << (lx + ly + lz);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 6 * per;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int comp = (int)(t / per);
+        int64_t r = t - comp * per;
+        const int qx = (int)(r % hx);
+        r /= hx;
+        const int qy = (int)(r % hy), qz = (int)(r / hy);
+        const int px = (int)brev_bits((unsigned)octant_freq(qx, lx), lx);
+        const int py = (int)brev_bits((unsigned)octant_freq(qy, ly), ly);
+        const int pz = (int)brev_bits((unsigned)octant_freq(qz, lz), lz);
+        const double2 v = full[comp * vol + (((int64_t)pz << ly) + py) * ((int64_t)1 << lx) + px];
+        oct[t] = cmk<C>(v.x, v.y);
+    }
+}
+
+int spectrum_build(const BoxSet& bs, double k0, double h, double2* oct128, float2* oct64, float2* full64,
+                   cudaStream_t s) {
+    const int64_t n = 6 * bs.spec_elems();
+    double2* G = nullptr;
+    VIE_CK(cudaMallocAsync((void**)&G, n * sizeof(double2), s));
+    int rc = green_sample(bs, k0, h, G, s);
+    if (!rc) rc = spectrum_fft<double2>(bs, G, s);
+    const int64_t no = 6 * bs.oct_elems();
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((no + 255) / 256, 152 * 16));
+    if (!rc && oct128) {
+        prof_begin(s, PK_SPECTRUM, VIE_C128, 0, no * 32, false);
+        k_octant_compress<double2><<<grid, 256, 0, s>>>(G, oct128, bs.lx, bs.ly, bs.lz);
+        prof_end(s);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(VIE_ECUDA, "octant compression launch failed");
+    }
+    if (!rc && oct64) {
+        prof_begin(s, PK_SPECTRUM, VIE_C64, 0, no * 24, false);
+        k_octant_compress<float2><<<grid, 256, 0, s>>>(G, oct64, bs.lx, bs.ly, bs.lz);
+        prof_end(s);
+        if (cudaGetLastError() != cudaSuccess) rc = fail(VIE_ECUDA, "octant compression launch failed");
+    }
+    if (!rc && full64) rc = convert_c128_to_c64(G, full64, n, s);
+    cudaError_t e = cudaFreeAsync(G, s);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync", __FILE__, __LINE__);
+    return rc;
 }
 
 template int mvm_boxes<double2>(const BoxSet&, const double2*, const double2*, double2*, const SegState*, cudaStream_t,

@@ -83,11 +83,49 @@ struct BoxSet {
     void* w1 = nullptr;                // [nb][3][bz][by][Mx] (sized for complex128)
     void* w2 = nullptr;                // [nb][3][bz][My][Mx]
     std::vector<int> block_ids;        // compact block index of each box
+    bool oct = false;                  // the MVM reads octant-compressed spectra (octant_slot)
 
     int64_t box_elems() const { return (int64_t)bx * by * bz; }
     int64_t vec_elems() const { return 3 * box_elems(); }             // per box
-    int64_t spec_elems() const { return (int64_t)Mx * My * Mz; }      // per component
+    int64_t spec_elems() const { return (int64_t)Mx * My * Mz; }      // per component, full
+    int64_t oct_elems() const {                                       // per component, octant
+        return (int64_t)(Mx / 2 + 1) * (My / 2 + 1) * (Mz / 2 + 1);
+    }
 };
+
+// Octant compression of a Green spectrum. Each component of the padded kernel
+// is even or odd under m -> M - m along each axis (xx, yy, zz even; xy odd in
+// x and y; xz odd in x and z; yz odd in y and z), so its DFT has the same
+// parity and is fixed by the frequencies f in [0, M/2] of every axis. Along an
+// axis of length M = 2^l, the spectrum entry at bit-reversed position p has
+// frequency k = brev_l(p); it is stored at slot q of the folded frequency
+// f = min(k, M - k), with q = brev_{l-1}(f) for f < M/2 and q = M/2 for
+// f = M/2 (the two positions 2j, 2j+1 of a warp then read runs of contiguous
+// slots), and `upper` (k > M/2) flips the sign of components odd along the axis.
+__host__ __device__ __forceinline__ unsigned bit_reverse(unsigned v, int l) {
+    unsigned r = 0;
+    for (int i = 0; i < l; ++i) r |= ((v >> i) & 1u) << (l - 1 - i);
+    return r;
+}
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ unsigned brev_bits(unsigned v, int l) { return l ? __brev(v) >> (32 - l) : 0u; }
+#else
+inline unsigned brev_bits(unsigned v, int l) { return bit_reverse(v, l); }
+#endif
+__host__ __device__ __forceinline__ int octant_slot(int p, int l, bool& upper) {
+    const int M = 1 << l, H = M >> 1;
+    const int k = (int)brev_bits((unsigned)p, l);
+    upper = k > H;
+    const int f = upper ? M - k : k;
+    if (f == H) return H;
+    return l >= 2 ? (int)brev_bits((unsigned)f, l - 1) : 0;
+}
+// frequency f of slot q (inverse of octant_slot on [0, M/2])
+__host__ __device__ __forceinline__ int octant_freq(int q, int l) {
+    const int H = (1 << l) >> 1;
+    if (q == H) return H;
+    return l >= 2 ? (int)brev_bits((unsigned)q, l - 1) : 0;
+}
 
 // Per-segment BiCGSTAB state (FP64 scalars on the device).
 enum SegStatus : int {
@@ -211,6 +249,11 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
               cudaStream_t s, const Twiddles* tw = nullptr, const C* const* Gb = nullptr);
 template <class C>
 int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* tw = nullptr);   // in place, 6 components
+// Green spectrum of one box shape at wavenumber k0 (FP64 samples and FFT in a
+// stream-ordered temporary), written to any of: oct128 / oct64 (octant
+// layout [6][Mz/2+1][My/2+1][Mx/2+1]), full64 (full layout [6][Mz][My][Mx]).
+int spectrum_build(const BoxSet& bs, double k0, double h, double2* oct128, float2* oct64, float2* full64,
+                   cudaStream_t s);
 
 // ---------------------------------------------------------------- green.cu
 int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t s);
