@@ -18,14 +18,16 @@
 // Each pass stages a tile of pencils in shared memory; global accesses are
 // along the contiguous x axis in every pass.
 #include <algorithm>
+#include <type_traits>
 
 #include "fft_core.cuh"
+#include "fft_reg.cuh"
 #include "vie_internal.cuh"
 
 namespace vie {
 
 constexpr int kThreads = 256;
-constexpr int kSmemBudget = 64 * 1024;
+constexpr int kSmemBudget = 32 * 1024;
 
 __device__ __forceinline__ bool box_active(const SegState* st, int b) {
     return st == nullptr || st[b].status == SEG_ACTIVE;
@@ -218,6 +220,115 @@ __global__ void __launch_bounds__(kThreads) k_zgreen(ZArgs<C> a) {
     }
 }
 
+// Pass Z of complex64 MVMs with Mz <= 32, register-resident: each thread
+// transforms one (component, column) pencil in registers (pruned: the box
+// fills at most the lower half of the padded axis), the three transformed
+// components of kZRegCols columns meet in shared memory for the 3x3 Green
+// multiply, and each thread transforms its pencil back, keeping z < bz. The
+// spectrum is even in z for xx, xy, yy, zz and odd for xz, yz, so one load of
+// its six entries serves the z positions of frequencies f and -f.
+constexpr int kZRegCols = 64;
+constexpr int kZRegThreads = 3 * kZRegCols;
+
+template <int LZ>
+__global__ void __launch_bounds__(kZRegThreads) k_zgreen_reg(ZArgs<float2> a) {
+    typedef float2 F;
+    constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1;
+    constexpr int LGZ = ILog2<LZ>::v;
+    constexpr int NC = kZRegCols;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    F* sm = reinterpret_cast<F*>(smem_raw);          // [3][LZ][NC]
+    const int b = blockIdx.y;
+    if (!box_active(a.st, b)) return;
+    if (a.units != nullptr && threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(a.units, 1);
+    const int P = a.ncols, bz = a.nzb, c0 = blockIdx.x * NC, t = threadIdx.x;
+    const int nc = min(NC, P - c0);
+    F* W = a.w + (int64_t)b * a.box_stride + c0;
+    const int64_t cs = a.comp_stride;
+    {
+        const int comp = t / NC, c = t - comp * NC;
+        if (c < nc) {
+            const F* src = W + comp * cs + c;
+            F* S = sm + comp * LZ * NC + c;
+            if (LZ == 1) {
+                S[0] = src[0];
+            } else {
+                F v[H];
+#pragma unroll
+                for (int j = 0; j < H; ++j) v[j] = j < bz ? src[(int64_t)j * P] : czero<F>();
+                F q[H];
+#pragma unroll
+                for (int j = 0; j < H; ++j) q[j] = twc<true>(v[j], j * (kLmax / LZ));
+                rfft<H, true>(q, (const F*)nullptr);
+#pragma unroll
+                for (int j = 0; j < H; ++j) S[(H + j) * NC] = q[j];
+                rfft<H, true>(v, (const F*)nullptr);
+#pragma unroll
+                for (int j = 0; j < H; ++j) S[j * NC] = v[j];
+            }
+        }
+    }
+    __syncthreads();
+    const F* G = a.Gb ? a.Gb[b] : a.G;
+    const int hx = (1 << a.lx) / 2 + 1, hy = (1 << a.ly) / 2 + 1;
+    const int cst = LZ * NC;
+    for (int task = t; task < LZ * NC; task += kZRegThreads) {
+        const int i = task / NC, c = task - i * NC;
+        if (c >= nc) continue;
+        const int f = LGZ ? (int)(__brev((unsigned)i) >> (32 - LGZ)) : 0;
+        const int fm = (LZ - f) & (LZ - 1);
+        const int im = LGZ ? (int)(__brev((unsigned)fm) >> (32 - LGZ)) : 0;
+        if (im < i) continue;
+        const int col = c0 + c;
+        bool ux, uy, uz;
+        const int qx = octant_slot(col & ((1 << a.lx) - 1), a.lx, ux);
+        const int qy = octant_slot(col >> a.lx, a.ly, uy);
+        const int qz = octant_slot(i, LGZ, uz);
+        const F* gp = G + ((int64_t)qz * hy + qy) * hx + qx;
+        const F gxx = gp[0], gyy = gp[3 * a.gcomp], gzz = gp[5 * a.gcomp];
+        F gxy = gp[a.gcomp], gxz = gp[2 * a.gcomp], gyz = gp[4 * a.gcomp];
+        if (ux != uy) gxy = mk(-gxy.x, -gxy.y);
+        if (ux != uz) gxz = mk(-gxz.x, -gxz.y);
+        if (uy != uz) gyz = mk(-gyz.x, -gyz.y);
+        {
+            F* q = sm + i * NC + c;
+            const F X = q[0], Y = q[cst], Z = q[2 * cst];
+            q[0] = cmul(gxx, X) + cmul(gxy, Y) + cmul(gxz, Z);
+            q[cst] = cmul(gxy, X) + cmul(gyy, Y) + cmul(gyz, Z);
+            q[2 * cst] = cmul(gxz, X) + cmul(gyz, Y) + cmul(gzz, Z);
+        }
+        if (im != i) {   // frequency -f: xz and yz change sign
+            F* q = sm + im * NC + c;
+            const F X = q[0], Y = q[cst], Z = q[2 * cst];
+            q[0] = cmul(gxx, X) + cmul(gxy, Y) - cmul(gxz, Z);
+            q[cst] = cmul(gxy, X) + cmul(gyy, Y) - cmul(gyz, Z);
+            q[2 * cst] = cmul(gzz, Z) - cmul(gxz, X) - cmul(gyz, Y);
+        }
+    }
+    __syncthreads();
+    {
+        const int comp = t / NC, c = t - comp * NC;
+        if (c < nc) {
+            F* S = sm + comp * LZ * NC + c;
+            F* dst = W + comp * cs + c;
+            if (LZ == 1) {
+                dst[0] = S[0];
+            } else {
+                F u[H], v[H];
+#pragma unroll
+                for (int j = 0; j < H; ++j) v[j] = S[(H + j) * NC];
+                rfft<H, false>(v, (const F*)nullptr);
+#pragma unroll
+                for (int j = 0; j < H; ++j) u[j] = S[j * NC];
+                rfft<H, false>(u, (const F*)nullptr);
+#pragma unroll
+                for (int j = 0; j < H; ++j)
+                    if (j < bz) dst[(int64_t)j * P] = u[j] + twc<false>(v[j], j * (kLmax / LZ));
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host side
 static int ilog2(int v) {
     int l = 0;
@@ -282,8 +393,32 @@ static int launch_cols(ColArgs<C> a, int nb1, int nb2, Prof pf, cudaStream_t s) 
     return VIE_OK;
 }
 
+template <int LZ>
+static int launch_zgreen_reg(ZArgs<float2> a, int nb, Prof pf, cudaStream_t s) {
+    const size_t smem = (size_t)3 * LZ * kZRegCols * sizeof(float2);
+    VIE_TRY(prep_smem(k_zgreen_reg<LZ>, smem));
+    dim3 grid((a.ncols + kZRegCols - 1) / kZRegCols, nb);
+    a.units = prof_begin(s, pf.kind, VIE_C64, pf.bpu, pf.fixed, true);
+    k_zgreen_reg<LZ><<<grid, kZRegThreads, smem, s>>>(a);
+    prof_end(s);
+    VIE_CK(cudaGetLastError());
+    return VIE_OK;
+}
+
 template <class C>
 static int launch_zgreen(ZArgs<C> a, int nb, Prof pf, cudaStream_t s) {
+    if constexpr (std::is_same<C, float2>::value) {
+        if (a.oct && a.lL <= 5) {   // register path: complex64, octant spectrum, Mz <= 32
+            switch (a.lL) {
+                case 0: return launch_zgreen_reg<1>(a, nb, pf, s);
+                case 1: return launch_zgreen_reg<2>(a, nb, pf, s);
+                case 2: return launch_zgreen_reg<4>(a, nb, pf, s);
+                case 3: return launch_zgreen_reg<8>(a, nb, pf, s);
+                case 4: return launch_zgreen_reg<16>(a, nb, pf, s);
+                default: return launch_zgreen_reg<32>(a, nb, pf, s);
+            }
+        }
+    }
     a.ltc = pick_ltile(a.lL, sizeof(C), 3, 0);
     if ((1 << a.ltc) > a.ncols) a.ltc = ilog2(a.ncols) - ((1 << ilog2(a.ncols)) > a.ncols ? 1 : 0);
     if (a.ltc < 0) a.ltc = 0;
@@ -350,6 +485,7 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     z.axis = planeXY; z.comp_stride = (int64_t)bs.bz * planeXY; z.box_stride = 3 * z.comp_stride;
     z.gcomp = bs.oct ? bs.oct_elems() : (int64_t)bs.Mz * planeXY;
     z.oct = bs.oct ? 1 : 0; z.lx = bs.lx; z.ly = bs.ly;
+    if (sizeof(C) == sizeof(float2) && bs.oct && bs.lz <= 5) VIE_TRY(reg_twiddles_ready(tw));
     VIE_TRY(launch_zgreen<C>(z, bs.nb, pz, s));
 
     // pass Y inverse: keep y < by

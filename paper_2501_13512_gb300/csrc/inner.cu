@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "fft_core.cuh"
+#include "fft_reg.cuh"
 #include "vie_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -270,93 +271,6 @@ __device__ void phase_xy_inv(const InnerGroup<C>& g, int64_t voff, const C* W, c
 }
 
 // ---------------------------------------------------------------- register-FFT box MVM (complex64)
-// Radix-2 FFT of one pencil held in registers, fully unrolled. FWD: natural
-// order in, bit-reversed out (decimation in frequency); !FWD: bit-reversed in,
-// natural out, unnormalised (decimation in time). Same ordering as the
-// shared-memory passes, so spectra from either path are interchangeable.
-template <bool FWD, class C>
-__device__ __forceinline__ C twmul(C v, int m, const C* __restrict__ tw) {
-    if (m == 0) return v;
-    if (m == kLmax / 4) return FWD ? mul_mi(v) : mul_i(v);
-    C w = __ldg(&tw[m]);
-    return FWD ? cmul(v, w) : cmulc(v, w);
-}
-
-template <int L> struct ILog2 { static constexpr int v = 1 + ILog2<L / 2>::v; };
-template <> struct ILog2<1> { static constexpr int v = 0; };
-
-// Twiddle multiply used by the register FFTs (specialised below per precision).
-template <class C> struct TwSel;
-
-// One radix-2 stage of span S (a compile-time constant) on an L-point pencil.
-template <int L, int S, bool FWD, class C>
-__device__ __forceinline__ void rstage(C (&a)[L], const C* __restrict__ tw) {
-#pragma unroll
-    for (int g = 0; g < L; g += 2 * S) {
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-            const int m = j * (kLmax / (2 * S));
-            if (FWD) {
-                C x0 = a[g + j], x1 = a[g + j + S];
-                a[g + j] = x0 + x1;
-                a[g + j + S] = TwSel<C>::template apply<true>(x0 - x1, m, tw);
-            } else {
-                C x0 = a[g + j], x1 = TwSel<C>::template apply<false>(a[g + j + S], m, tw);
-                a[g + j] = x0 + x1;
-                a[g + j + S] = x0 - x1;
-            }
-        }
-    }
-}
-
-// Stages with spans S, S/2, ..., 1 (forward) or S, 2S, ..., L/2 (inverse).
-template <int L, int S, bool FWD> struct RStages {
-    template <class C> static __device__ __forceinline__ void run(C (&a)[L], const C* __restrict__ tw) {
-        rstage<L, S, FWD>(a, tw);
-        RStages<L, FWD ? S / 2 : S * 2, FWD>::run(a, tw);
-    }
-};
-template <int L> struct RStages<L, 0, true> {
-    template <class C> static __device__ __forceinline__ void run(C (&)[L], const C* __restrict__) {}
-};
-template <int L> struct RStages<L, L, false> {
-    template <class C> static __device__ __forceinline__ void run(C (&)[L], const C* __restrict__) {}
-};
-
-template <int L, bool FWD, class C>
-__device__ __forceinline__ void rfft(C (&a)[L], const C* __restrict__ tw) {
-    if (L < 2) return;
-    RStages<L, FWD ? L / 2 : 1, FWD>::run(a, tw);
-}
-
-typedef float2 F;
-
-// Twiddles W_Lmax^m of the complex64 register path in constant memory: the
-// register FFTs index them with compile-time offsets, so they become constant
-// operands instead of loads. Copied once per device before the first launch.
-__constant__ F c_tw64[kLmax];
-
-template <bool FWD>
-__device__ __forceinline__ F twc(F v, int m) {
-    if (m == 0) return v;
-    if (m == kLmax / 4) return FWD ? mul_mi(v) : mul_i(v);
-    F w = c_tw64[m];
-    return FWD ? cmul(v, w) : cmulc(v, w);
-}
-
-template <> struct TwSel<double2> {
-    template <bool FWD>
-    static __device__ __forceinline__ double2 apply(double2 v, int m, const double2* __restrict__ tw) {
-        return twmul<FWD>(v, m, tw);
-    }
-};
-template <> struct TwSel<float2> {
-    template <bool FWD>
-    static __device__ __forceinline__ float2 apply(float2 v, int m, const float2* __restrict__) {
-        return twc<FWD>(v, m);
-    }
-};
-
 // Division by a runtime divisor d (1 <= d < 2^31) of n < 2^31 with a multiply-high
 // (Granlund and Montgomery, PLDI 1994): q = (umulhi(n, m) + n) >> s.
 struct FastDiv {
@@ -380,59 +294,6 @@ constexpr int kPf = 2;   // iterations ahead
 constexpr int kU = 1;   // elements per thread whose loads are issued together in the row phases
 constexpr int kUV = 1;  // elements per thread per batch in the block-vector passes
 constexpr int kUG = 1;  // Green-multiply tasks per thread whose 6 spectrum loads are issued together
-
-// Pruned transforms. A box of b voxels is padded to L >= 2b - 1, a power of
-// two, so b <= L/2: forward inputs beyond L/2 are zero and inverse outputs
-// beyond L/2 are discarded. The first DIF stage then splits the L-point
-// transform into FFT_{L/2}(x) (positions [0, L/2)) and FFT_{L/2}(x_j W_L^j)
-// (positions [L/2, L)); the last DIT stage of the inverse combines
-// u = iFFT_{L/2}(lower half) and v = iFFT_{L/2}(upper half) as
-// u_j + conj(W_L^j) v_j. Only L/2 values are live in registers at a time.
-
-// Forward: get(j) gives input j < L/2 (zero where the box ends); put(k, v)
-// receives output position k (bit-reversed order).
-template <int L, class Get, class Put>
-__device__ __forceinline__ void fwd_half(Get get, Put put, const F* __restrict__ tw) {
-    if (L == 1) {
-        put(0, get(0));
-        return;
-    }
-    constexpr int H = L / 2 > 0 ? L / 2 : 1;
-    F a[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) a[j] = twc<true>(get(j), j * (kLmax / L));
-    rfft<H, true>(a, tw);
-#pragma unroll
-    for (int j = 0; j < H; ++j) put(H + j, a[j]);
-#pragma unroll
-    for (int j = 0; j < H; ++j) a[j] = get(j);
-    rfft<H, true>(a, tw);
-#pragma unroll
-    for (int j = 0; j < H; ++j) put(j, a[j]);
-}
-
-// Inverse keeping outputs [0, L/2): get(k) gives input position k;
-// stash(j, v) / unstash(j) hold conj(W_L^j) v_j between the two halves;
-// put(j, v) receives output j (called for every j < L/2).
-template <int L, class Get, class Stash, class Unstash, class Put>
-__device__ __forceinline__ void inv_half(Get get, Stash stash, Unstash unstash, Put put, const F* __restrict__ tw) {
-    if (L == 1) {
-        put(0, get(0));
-        return;
-    }
-    constexpr int H = L / 2 > 0 ? L / 2 : 1;
-    F a[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) a[j] = get(H + j);
-    rfft<H, false>(a, tw);
-#pragma unroll
-    for (int j = 0; j < H; ++j) stash(j, twc<false>(a[j], j * (kLmax / L)));
-#pragma unroll
-    for (int j = 0; j < H; ++j) a[j] = get(j);
-    rfft<H, false>(a, tw);
-#pragma unroll
-    for (int j = 0; j < H; ++j) put(j, a[j] + unstash(j));
-}
 
 // X forward: rows (component, z, y) of the box. Coalesced loads (with the
 // BiCGSTAB update fused) into IN, one pruned row FFT per thread into OUT,
@@ -985,8 +846,6 @@ static void make_fastdiv(unsigned d, unsigned (&out)[3]) {
     out[2] = d;
 }
 
-static std::mutex g_ctw_mu;
-static std::vector<int> g_ctw_dev;
 
 bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force) {
     int a, b;
@@ -1039,16 +898,7 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         smem = std::max(smem, sm);
         bytes_per_block = std::max<int64_t>(bytes_per_block, 3 * bs.box_elems() * (int64_t)sizeof(C));
     }
-    {
-        // constant-memory twiddles of the register path, once per device
-        int dev = 0;
-        VIE_CK(cudaGetDevice(&dev));
-        std::lock_guard<std::mutex> lock(g_ctw_mu);
-        if (std::find(g_ctw_dev.begin(), g_ctw_dev.end(), dev) == g_ctw_dev.end()) {
-            VIE_CK(cudaMemcpyToSymbol(c_tw64, tw.d64, kLmax * sizeof(float2), 0, cudaMemcpyDeviceToDevice));
-            g_ctw_dev.push_back(dev);
-        }
-    }
+    VIE_TRY(reg_twiddles_ready(tw));   // constant-memory twiddles of the register path
     VIE_CK(cudaMemcpyAsync(d_groups, hg.data(), hg.size() * sizeof(InnerGroup<C>), cudaMemcpyHostToDevice, s));
     VIE_CK(cudaMemsetAsync(d_next, 0, sizeof(int), s));
     // opt in to the exact dynamic size: the default 48 KB limit also counts the static shared memory
