@@ -329,6 +329,231 @@ __global__ void __launch_bounds__(kZRegThreads) k_zgreen_reg(ZArgs<float2> a) {
     }
 }
 
+// ---------------------------------------------------------------- four-step register passes (complex64)
+// An L = 32 A point transform (A = 2 .. 32) of a line as two register passes
+// with one shared-memory exchange, instead of log2 L shared-memory stages.
+// Forward (decimation in frequency, natural -> bit-reversed, as smem_fft):
+//   step A  thread j < 32 holds the positions j + 32 m (m < A) and applies the
+//           radix-2 stages of spans L/2 .. 32; the pair (p, p + S) with p =
+//           j + 32 mm (mm < S/32) takes the twiddle W_L^{p L/(2S)}, which is
+//           W_Lmax^{16 j / s} W_Lmax^{512 mm / s} with s = S/32: one runtime
+//           factor per stage and a compile-time one per pair;
+//   step B  thread g < A holds the 32 positions 32 g + r and applies the
+//           stages of spans 16 .. 1: a 32-point transform with compile-time
+//           twiddles (rfft<32>).
+// Inverse (decimation in time, bit-reversed -> natural): step B then step A,
+// with conjugate twiddles in reverse span order. Inputs of the forward pass
+// are zero beyond L/2 and outputs of the inverse pass beyond L/2 are dropped
+// (pruning: a box of n voxels is padded to L >= 2n - 1).
+constexpr int kB4 = 32;
+
+template <int A>
+__device__ __forceinline__ void step_a_fwd(float2 (&v)[A], int j, const float2* __restrict__ tw) {
+#pragma unroll
+    for (int sp = A / 2; sp >= 1; sp >>= 1) {
+        const float2 wj = __ldg(&tw[(16 * j) / sp]);
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+            if ((m & sp) != 0) continue;
+            const int mm = m & (sp - 1);
+            const float2 x0 = v[m], x1 = v[m + sp];
+            v[m] = x0 + x1;
+            v[m + sp] = twc<true>(cmul(x0 - x1, wj), (512 / sp) * mm);
+        }
+    }
+}
+
+// Inverse step A; only the outputs m < A/2 are formed by the last stage.
+template <int A>
+__device__ __forceinline__ void step_a_inv(float2 (&v)[A], int j, const float2* __restrict__ tw) {
+#pragma unroll
+    for (int sp = 1; sp <= A / 2; sp <<= 1) {
+        const float2 wj = __ldg(&tw[(16 * j) / sp]);
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+            if ((m & sp) != 0) continue;
+            const int mm = m & (sp - 1);
+            const float2 x0 = v[m];
+            const float2 x1 = cmulc(twc<false>(v[m + sp], (512 / sp) * mm), wj);
+            v[m] = x0 + x1;
+            if (sp < A / 2) v[m + sp] = x0 - x1;
+        }
+    }
+}
+
+// shared-memory index of position p of a line: one pad per 32 positions
+__device__ __forceinline__ int pad32(int p) { return p + (p >> 5); }
+
+constexpr int kRows4 = 8;   // rows per CTA (256 threads: 8 rows x 32)
+
+// Pass X forward: rows of bx -> chi * x, zero-padded to L = 32 A, forward transform.
+template <int A>
+__global__ void __launch_bounds__(256) k_rows4_fwd(RowArgs<float2> a) {
+    constexpr int L = kB4 * A, LP = L + L / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);     // [kRows4][LP]
+    const int64_t row0 = (int64_t)blockIdx.x * kRows4;
+    if (a.units != nullptr && threadIdx.x == 0) {
+        const int64_t rpb = a.rows_per_box;
+        for (int64_t b = (row0 + rpb - 1) / rpb; b * rpb < row0 + kRows4 && b * rpb < a.nrows; ++b)
+            if (box_active(a.st, (int)b)) atomicAdd(a.units, 1);
+    }
+    {
+        const int r = threadIdx.x >> 5, j = threadIdx.x & 31;
+        const int64_t row = row0 + r;
+        float2 v[A];
+        bool live = row < a.nrows;
+        int b = 0;
+        if (live) {
+            b = (int)(row / a.rows_per_box);
+            live = box_active(a.st, b);
+        }
+        const int64_t crow = live ? (int64_t)b * a.plane + (row % a.plane) : 0;
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+            v[m] = czero<float2>();
+            const int p = j + kB4 * m;
+            if (m < A / 2 && live && p < a.n_in) v[m] = cmul(a.in[row * a.in_stride + p], a.chi[crow * a.bx + p]);
+        }
+        step_a_fwd<A>(v, j, a.tw);
+#pragma unroll
+        for (int m = 0; m < A; ++m) sm[r * LP + pad32(j + kB4 * m)] = v[m];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kRows4 * A; t += blockDim.x) {
+        const int r = t / A, g = t - r * A;
+        float2* q = sm + r * LP + g * (kB4 + 1);
+        float2 u[kB4];
+#pragma unroll
+        for (int i = 0; i < kB4; ++i) u[i] = q[i];
+        rfft<kB4, true>(u, (const float2*)nullptr);
+#pragma unroll
+        for (int i = 0; i < kB4; ++i) q[i] = u[i];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kRows4 * L; idx += blockDim.x) {
+        const int r = idx / L, p = idx - r * L;
+        const int64_t row = row0 + r;
+        if (row >= a.nrows || !box_active(a.st, (int)(row / a.rows_per_box))) continue;
+        a.out[row * a.out_stride + p] = sm[r * LP + pad32(p)];
+    }
+}
+
+// Pass X inverse: rows of L = 32 A spectrum positions -> keep x < bx, y = mask (x - u).
+template <int A>
+__global__ void __launch_bounds__(256) k_rows4_inv(RowArgs<float2> a) {
+    constexpr int L = kB4 * A, LP = L + L / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);     // [kRows4][LP]
+    const int64_t row0 = (int64_t)blockIdx.x * kRows4;
+    if (a.units != nullptr && threadIdx.x == 0) {
+        const int64_t rpb = a.rows_per_box;
+        for (int64_t b = (row0 + rpb - 1) / rpb; b * rpb < row0 + kRows4 && b * rpb < a.nrows; ++b)
+            if (box_active(a.st, (int)b)) atomicAdd(a.units, 1);
+    }
+    for (int idx = threadIdx.x; idx < kRows4 * L; idx += blockDim.x) {
+        const int r = idx / L, p = idx - r * L;
+        const int64_t row = row0 + r;
+        float2 v = czero<float2>();
+        if (row < a.nrows && box_active(a.st, (int)(row / a.rows_per_box))) v = a.in[row * a.in_stride + p];
+        sm[r * LP + pad32(p)] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kRows4 * A; t += blockDim.x) {
+        const int r = t / A, g = t - r * A;
+        float2* q = sm + r * LP + g * (kB4 + 1);
+        float2 u[kB4];
+#pragma unroll
+        for (int i = 0; i < kB4; ++i) u[i] = q[i];
+        rfft<kB4, false>(u, (const float2*)nullptr);
+#pragma unroll
+        for (int i = 0; i < kB4; ++i) q[i] = u[i];
+    }
+    __syncthreads();
+    const int r = threadIdx.x >> 5, j = threadIdx.x & 31;
+    const int64_t row = row0 + r;
+    if (row >= a.nrows) return;
+    const int b = (int)(row / a.rows_per_box);
+    if (!box_active(a.st, b)) return;
+    float2 v[A];
+#pragma unroll
+    for (int m = 0; m < A; ++m) v[m] = sm[r * LP + pad32(j + kB4 * m)];
+    step_a_inv<A>(v, j, a.tw);
+    const int64_t mrow = (int64_t)b * a.plane + (row % a.plane);
+#pragma unroll
+    for (int m = 0; m < A / 2; ++m) {
+        const int p = j + kB4 * m;
+        if (p >= a.n_out) continue;
+        const int64_t o = row * a.out_stride + p;
+        float2 y = a.xin[o] - v[m];
+        if (a.mask != nullptr && !a.mask[mrow * a.bx + p]) y = czero<float2>();
+        a.out[o] = y;
+    }
+}
+
+constexpr int kCols4 = 16;   // columns per CTA (512 threads: 16 columns x 32)
+
+// Pass Y (forward or inverse) over columns of L = 32 A, 16 adjacent columns per CTA.
+template <int A, bool FWD>
+__global__ void __launch_bounds__(512) k_cols4(ColArgs<float2> a) {
+    constexpr int L = kB4 * A;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);     // [L][kCols4]
+    const int col0 = blockIdx.x * kCols4;
+    if (!box_active(a.st, blockIdx.z / a.b2_per_box)) return;
+    if (a.units != nullptr && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 &&
+        blockIdx.z % a.b2_per_box == 0)
+        atomicAdd(a.units, 1);
+    const float2* in = a.in + blockIdx.z * a.in_s2 + blockIdx.y * a.in_s1 + col0;
+    float2* out = a.out + blockIdx.z * a.out_s2 + blockIdx.y * a.out_s1 + col0;
+    const int ncol = min(kCols4, a.ncols - col0);
+    const int c = threadIdx.x % kCols4, k = threadIdx.x / kCols4;    // k: j (step A) or g (step B)
+    if (FWD) {
+        if (c < ncol) {
+            float2 v[A];
+#pragma unroll
+            for (int m = 0; m < A; ++m) {
+                const int p = k + kB4 * m;
+                v[m] = (m < A / 2 && p < a.n_in) ? in[p * a.in_axis + c] : czero<float2>();
+            }
+            step_a_fwd<A>(v, k, a.tw);
+#pragma unroll
+            for (int m = 0; m < A; ++m) sm[(k + kB4 * m) * kCols4 + c] = v[m];
+        }
+        __syncthreads();
+        if (k < A && c < ncol) {
+            float2 u[kB4];
+#pragma unroll
+            for (int i = 0; i < kB4; ++i) u[i] = sm[(kB4 * k + i) * kCols4 + c];
+            rfft<kB4, true>(u, (const float2*)nullptr);
+#pragma unroll
+            for (int i = 0; i < kB4; ++i)
+                if (kB4 * k + i < a.n_out) out[(kB4 * k + i) * a.out_axis + c] = u[i];
+        }
+    } else {
+        if (k < A && c < ncol) {
+            float2 u[kB4];
+#pragma unroll
+            for (int i = 0; i < kB4; ++i) u[i] = in[(kB4 * k + i) * a.in_axis + c];
+            rfft<kB4, false>(u, (const float2*)nullptr);
+#pragma unroll
+            for (int i = 0; i < kB4; ++i) sm[(kB4 * k + i) * kCols4 + c] = u[i];
+        }
+        __syncthreads();
+        if (c < ncol) {
+            float2 v[A];
+#pragma unroll
+            for (int m = 0; m < A; ++m) v[m] = sm[(k + kB4 * m) * kCols4 + c];
+            step_a_inv<A>(v, k, a.tw);
+#pragma unroll
+            for (int m = 0; m < A / 2; ++m) {
+                const int p = k + kB4 * m;
+                if (p < a.n_out) out[p * a.out_axis + c] = v[m];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host side
 static int ilog2(int v) {
     int l = 0;
@@ -362,8 +587,42 @@ struct Prof {
 };
 template <class C> static int prec_code() { return sizeof(C) == 16 ? VIE_C128 : VIE_C64; }
 
+template <int A, bool FWD>
+static int launch_rows4(RowArgs<float2> a, Prof pf, cudaStream_t s) {
+    constexpr int L = kB4 * A;
+    const size_t smem = (size_t)kRows4 * (L + L / 32) * sizeof(float2);
+    auto kern = FWD ? k_rows4_fwd<A> : k_rows4_inv<A>;
+    VIE_TRY(prep_smem(kern, smem));
+    const int64_t grid = (a.nrows + kRows4 - 1) / kRows4;
+    if (grid <= 0) return VIE_OK;
+    a.units = prof_begin(s, pf.kind, VIE_C64, pf.bpu, pf.fixed, true);
+    kern<<<(unsigned)grid, 256, smem, s>>>(a);
+    prof_end(s);
+    VIE_CK(cudaGetLastError());
+    return VIE_OK;
+}
+
+template <bool FWD>
+static int launch_rows4_any(RowArgs<float2> a, Prof pf, cudaStream_t s) {
+    switch (a.lL) {
+        case 6: return launch_rows4<2, FWD>(a, pf, s);
+        case 7: return launch_rows4<4, FWD>(a, pf, s);
+        case 8: return launch_rows4<8, FWD>(a, pf, s);
+        case 9: return launch_rows4<16, FWD>(a, pf, s);
+        default: return launch_rows4<32, FWD>(a, pf, s);
+    }
+}
+
 template <class C, int MODE>
 static int launch_rows(RowArgs<C> a, Prof pf, cudaStream_t s) {
+    if constexpr (std::is_same<C, float2>::value) {
+        // four-step register path: complex64 MVM rows of 64 .. 1024, pruned to half the length
+        const int L = 1 << a.lL;
+        if (a.lL >= 6 && a.lL <= kLogLmax) {
+            if (MODE == ROW_FWD_CHI && 2 * a.n_in <= L && a.n_out == L) return launch_rows4_any<true>(a, pf, s);
+            if (MODE == ROW_INV_UPDATE && 2 * a.n_out <= L && a.n_in == L) return launch_rows4_any<false>(a, pf, s);
+        }
+    }
     a.ltr = pick_ltile(a.lL, sizeof(C), 1, 1);
     const int TR = 1 << a.ltr;
     size_t smem = (size_t)(1 << a.lL) * (TR + 1) * sizeof(C);
@@ -377,8 +636,34 @@ static int launch_rows(RowArgs<C> a, Prof pf, cudaStream_t s) {
     return VIE_OK;
 }
 
+template <int A, bool FWD>
+static int launch_cols4(ColArgs<float2> a, int nb1, int nb2, Prof pf, cudaStream_t s) {
+    const size_t smem = (size_t)kB4 * A * kCols4 * sizeof(float2);
+    VIE_TRY(prep_smem(k_cols4<A, FWD>, smem));
+    dim3 grid((a.ncols + kCols4 - 1) / kCols4, nb1, nb2);
+    a.units = prof_begin(s, pf.kind, VIE_C64, pf.bpu, pf.fixed, true);
+    k_cols4<A, FWD><<<grid, kB4 * kCols4, smem, s>>>(a);
+    prof_end(s);
+    VIE_CK(cudaGetLastError());
+    return VIE_OK;
+}
+
 template <class C, bool FWD>
 static int launch_cols(ColArgs<C> a, int nb1, int nb2, Prof pf, cudaStream_t s) {
+    if constexpr (std::is_same<C, float2>::value) {
+        // four-step register path: complex64 columns of 64 .. 1024, pruned to half the length
+        const int L = 1 << a.lL;
+        if (a.lL >= 6 && a.lL <= kLogLmax && (FWD ? (2 * a.n_in <= L && a.n_out == L)
+                                                   : (2 * a.n_out <= L && a.n_in == L))) {
+            switch (a.lL) {
+                case 6: return launch_cols4<2, FWD>(a, nb1, nb2, pf, s);
+                case 7: return launch_cols4<4, FWD>(a, nb1, nb2, pf, s);
+                case 8: return launch_cols4<8, FWD>(a, nb1, nb2, pf, s);
+                case 9: return launch_cols4<16, FWD>(a, nb1, nb2, pf, s);
+                default: return launch_cols4<32, FWD>(a, nb1, nb2, pf, s);
+            }
+        }
+    }
     a.ltc = pick_ltile(a.lL, sizeof(C), 1, 0);
     if ((1 << a.ltc) > a.ncols) a.ltc = ilog2(a.ncols) - ((1 << ilog2(a.ncols)) > a.ncols ? 1 : 0);
     if (a.ltc < 0) a.ltc = 0;
@@ -444,6 +729,7 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     if (twp) tw = *twp;
     else VIE_TRY(get_twiddles(&tw));
     const C* T = tw_ptr<C>(tw);
+    if (sizeof(C) == sizeof(float2)) VIE_TRY(reg_twiddles_ready(tw));   // constant table of the register passes
     C* w1 = reinterpret_cast<C*>(bs.w1);
     C* w2 = reinterpret_cast<C*>(bs.w2);
     const int64_t planeXY = (int64_t)bs.Mx * bs.My;
@@ -485,7 +771,6 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     z.axis = planeXY; z.comp_stride = (int64_t)bs.bz * planeXY; z.box_stride = 3 * z.comp_stride;
     z.gcomp = bs.oct ? bs.oct_elems() : (int64_t)bs.Mz * planeXY;
     z.oct = bs.oct ? 1 : 0; z.lx = bs.lx; z.ly = bs.ly;
-    if (sizeof(C) == sizeof(float2) && bs.oct && bs.lz <= 5) VIE_TRY(reg_twiddles_ready(tw));
     VIE_TRY(launch_zgreen<C>(z, bs.nb, pz, s));
 
     // pass Y inverse: keep y < by
