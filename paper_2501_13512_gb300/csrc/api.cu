@@ -325,12 +325,14 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
             (prec == 0 ? gr.persistent128 : gr.persistent64) = ok;
             if (!ok) continue;
             for (int b = 0; b < gr.bs.nb; ++b) items.push_back({gr.bs.spec_elems(), make_int2(job, b)});
+            g->job_group[prec].push_back((int)(&gr - g->groups.data()));
             ++job;
         }
         std::stable_sort(items.begin(), items.end(),
                          [](const std::pair<int64_t, int2>& a, const std::pair<int64_t, int2>& b) { return a.first > b.first; });
         std::vector<int2> w;
         for (auto& it : items) w.push_back(it.second);
+        g->work_host[prec] = w;
         int2** dst = prec == 0 ? &g->work128 : &g->work64;
         (prec == 0 ? g->nwork128 : g->nwork64) = (int)w.size();
         if (!w.empty()) {
@@ -613,24 +615,45 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     }
     VIE_TRY(precond_copy_unblocked<C>(g, b, y, s));
     for (int i = 0; i < ng; ++i) VIE_TRY(precond_scatter_group<C>(g, g->groups[i], group_vecs<C>(g->groups[i]).x, y, s));
-    if (stats) {
-        std::vector<SegState> hs;
-        double sum = 0.0;
-        stats->nblocks = g->nblocks;
+    std::vector<int2>& wh = g->work_host[c128 ? 0 : 1];
+    const bool reorder = !jobs.empty() && wh.size() > 1;
+    if (stats || reorder) {
+        std::vector<std::vector<SegState>> hs(ng);
         for (int i = 0; i < ng; ++i) {
             Group& gr = g->groups[i];
-            hs.resize(gr.bs.nb);
-            VIE_CK(cudaMemcpyAsync(hs.data(), gr.st, gr.bs.nb * sizeof(SegState), cudaMemcpyDeviceToHost, s));
-            VIE_CK(cudaEventRecord(g->ev[0], s));
-            VIE_TRY(wait_event(g->ev[0], timeout_ms));
-            for (auto& st : hs) {
-                sum += st.iters;
-                stats->max_iters = std::max(stats->max_iters, (int32_t)std::ceil(st.iters));
-                if (st.status == SEG_MAXIT) stats->not_converged++;
-                if (st.status == SEG_BREAKDOWN) stats->breakdowns++;
-            }
+            hs[i].resize(gr.bs.nb);
+            VIE_CK(cudaMemcpyAsync(hs[i].data(), gr.st, gr.bs.nb * sizeof(SegState), cudaMemcpyDeviceToHost, s));
         }
-        stats->mean_iters = sum / std::max(1, g->nblocks);
+        VIE_CK(cudaEventRecord(g->ev[0], s));
+        VIE_TRY(wait_event(g->ev[0], timeout_ms));
+        if (stats) {
+            double sum = 0.0;
+            stats->nblocks = g->nblocks;
+            for (int i = 0; i < ng; ++i)
+                for (auto& st : hs[i]) {
+                    sum += st.iters;
+                    stats->max_iters = std::max(stats->max_iters, (int32_t)std::ceil(st.iters));
+                    if (st.status == SEG_MAXIT) stats->not_converged++;
+                    if (st.status == SEG_BREAKDOWN) stats->breakdowns++;
+                }
+            stats->mean_iters = sum / std::max(1, g->nblocks);
+        }
+        if (reorder) {
+            // longest-processing-time-first order for the next apply: the blocks' iteration counts
+            // of this apply (they change little from one apply to the next) x their padded box size
+            const std::vector<int>& jg = g->job_group[c128 ? 0 : 1];
+            std::vector<std::pair<double, int2>> items;
+            items.reserve(wh.size());
+            for (const int2& w : wh) {
+                const Group& gr = g->groups[jg[w.x]];
+                items.push_back({(hs[jg[w.x]][w.y].iters + 1.0) * (double)gr.bs.spec_elems(), w});
+            }
+            std::stable_sort(items.begin(), items.end(), [](const std::pair<double, int2>& a,
+                                                            const std::pair<double, int2>& b) { return a.first > b.first; });
+            for (size_t k = 0; k < items.size(); ++k) wh[k] = items[k].second;
+            VIE_CK(cudaMemcpyAsync(c128 ? g->work128 : g->work64, wh.data(), wh.size() * sizeof(int2),
+                                   cudaMemcpyHostToDevice, s));
+        }
     }
     if (tuning) {
         // score: persistent-launch time per iteration of its slowest block (the critical path)

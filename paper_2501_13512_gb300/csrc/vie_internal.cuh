@@ -212,6 +212,10 @@ struct vie_grid {
     int2* work128 = nullptr;
     int2* work64 = nullptr;
     int nwork128 = 0, nwork64 = 0;
+    // host copies of the work lists and the group of each job, per precision (0: c128, 1: c64);
+    // after every apply the list is re-sorted by the blocks' measured cost (longest first)
+    std::vector<int2> work_host[2];
+    std::vector<int> job_group[2];
     void* inner_groups = nullptr;         // device copy of the per-group descriptors
     int* inner_next = nullptr;            // work counter
     // cluster-size autotuning of the persistent solver, per precision (0: c128, 1: c64):
