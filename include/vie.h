@@ -167,7 +167,9 @@ typedef struct {
     double outer_tol;        /* stop when ||E_inc - A E|| <= outer_tol ||E_inc||   */
     double inner_tol;        /* block solves' relative tolerance (Section II.B)     */
     int32_t outer_maxit;     /* outer BiCGSTAB iterations (per refinement in MIXED) */
-    int32_t inner_maxit;     /* inner BiCGSTAB iterations per block apply           */
+    int32_t inner_maxit;     /* cap on inner BiCGSTAB iterations per block apply;
+                                a cap the blocks never reach (e.g. 1000) keeps K2
+                                a converged block inverse (metal blocks need ~350) */
     int32_t use_precond;     /* 0: unpreconditioned BiCGSTAB                        */
     int32_t mode;            /* vie_solve_mode                                      */
     int32_t max_refinements; /* MIXED: FP64 residual corrections, 0 = default (8)   */

@@ -51,7 +51,7 @@ def find_blocks(block_id):
 class BlockPreconditioner:
     """y = K2^{-1} b, each block solved inexactly by inner BiCGSTAB-FFT."""
 
-    def __init__(self, eps_r, block_id, h, k, inner_tol=1e-2, inner_maxit=100):
+    def __init__(self, eps_r, block_id, h, k, inner_tol=1e-2, inner_maxit=1000):
         self.blocks = find_blocks(block_id)
         self.ops = []
         for b in self.blocks:

@@ -35,7 +35,7 @@ def plane_wave(n, h, k, khat, pol):
 
 
 def solve(eps_r, block_id, h, k, einc, tol=1e-6, use_precond=True,
-          inner_tol=1e-2, inner_maxit=100, maxit=1000):
+          inner_tol=1e-2, inner_maxit=1000, maxit=1000):
     """Solve A E = E_inc; returns (E, info) with the true residual added to info."""
     A = FFTOperator(eps_r, h, k)
     Kinv = None

@@ -262,7 +262,7 @@ class Grid:
                                  self._vec(y, precision, "y"), _stream()))
         return y
 
-    def precond(self, spec, b, y=None, inner_tol=1e-2, inner_maxit=100, precision=None):
+    def precond(self, spec, b, y=None, inner_tol=1e-2, inner_maxit=1000, precision=None):
         precision = precision or (C128 if b.dtype == _dtype(C128) else C64)
         y = self.empty(precision) if y is None else y
         st = PrecondStats()
@@ -271,7 +271,7 @@ class Grid:
                                               _stream(), byref(st)))
         return y, _struct_dict(st)
 
-    def solve(self, spec, einc, e=None, outer_tol=1e-6, inner_tol=1e-2, outer_maxit=1000, inner_maxit=100,
+    def solve(self, spec, einc, e=None, outer_tol=1e-6, inner_tol=1e-2, outer_maxit=1000, inner_maxit=1000,
               use_precond=True, mode=MODE_MIXED, max_refinements=0, wait_timeout_ms=0.0, x0=None, check=True):
         """x0: initial guess (complex128 CUDA tensor, may be `e` itself), None for zero."""
         e = self.empty(C128) if e is None else e
