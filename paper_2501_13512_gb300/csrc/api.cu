@@ -163,6 +163,9 @@ static void release_grid(vie_grid* g) {
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
         if (g->tev[i]) cudaEventDestroy(g->tev[i]);
     }
+    if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+    if (g->join_ev) cudaEventDestroy(g->join_ev);
+    if (g->s2) cudaStreamDestroy(g->s2);
     delete g;
 }
 
@@ -345,7 +348,7 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
         char* descs = nullptr;
         if ((rc = dalloc(g, &descs, (int64_t)(g->groups.size() * inner_group_desc_bytes())))) return bail(rc);
         g->inner_groups = descs;
-        if ((rc = dalloc(g, &g->inner_next, 1))) return bail(rc);
+        if ((rc = dalloc(g, &g->inner_next, 2))) return bail(rc);
     }
     if ((rc = dalloc(g, &g->block_id, N))) return bail(rc);
     if (cudaMemcpy(g->block_id, bid.data(), N * 4, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -366,6 +369,10 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
         if (cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreate(&g->tev[i]) != cudaSuccess)
             return bail(fail(VIE_ECUDA, "cudaEventCreate failed"));
+    if (cudaStreamCreateWithFlags(&g->s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->join_ev, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(VIE_ECUDA, "stream or event creation failed"));
     *out = g;
     return VIE_OK;
 }
@@ -564,15 +571,22 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             batched.push_back(i);
         }
     }
-    // cluster size: candidates 2 and 4 tried on the first two applies, then the best
-    static const int kCand[2] = {2, 4};
+    // cluster size: candidates 2 and 4 for every block, then the split launch (4 for the slowest
+    // blocks of the previous apply, 2 for the rest), tried on the first three applies; then the best
+    static const int kCand[3] = {2, 4, -1};
     const int pi = c128 ? 0 : 1;
     const int tried = g->tune_count[pi];
-    const bool tuning = !jobs.empty() && tried < 2 && !inner_cluster_forced();
-    const int R = tuning ? kCand[tried] : (g->tune_best[pi] ? g->tune_best[pi] : 2);
+    const bool tuning = !jobs.empty() && tried < 3 && !inner_cluster_forced();
+    const int choice = tuning ? kCand[tried] : (g->tune_best[pi] ? g->tune_best[pi] : 2);
+    InnerSplit split;
+    split.nheavy = choice == -1 ? g->nheavy[pi] : 0;
+    split.cluster = 4;
+    split.s2 = g->s2;
+    split.fork = g->fork_ev;
+    split.join = g->join_ev;
     if (tuning) VIE_CK(cudaEventRecord(g->tev[0], s));
     VIE_TRY(inner_persistent<C>(jobs, c128 ? g->work128 : g->work64, c128 ? g->nwork128 : g->nwork64,
-                                g->inner_groups, g->inner_next, tol, maxit, s, R));
+                                g->inner_groups, g->inner_next, tol, maxit, s, choice == -1 ? 2 : choice, &split));
     if (tuning) VIE_CK(cudaEventRecord(g->tev[1], s));
     std::vector<Bicg<C>> bk(ng);
     for (int i : batched) {
@@ -651,6 +665,14 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             std::stable_sort(items.begin(), items.end(), [](const std::pair<double, int2>& a,
                                                             const std::pair<double, int2>& b) { return a.first > b.first; });
             for (size_t k = 0; k < items.size(); ++k) wh[k] = items[k].second;
+            // heavy part of a split launch: blocks that took at least 0.6 of the largest iteration
+            // count, at most an eighth of the blocks (measured on the metasurface: 0.5 / 4, 0.75 / 16
+            // and 0.9 / 32 were slower)
+            double itmax = 0.0;
+            for (const int2& w : wh) itmax = std::max(itmax, hs[jg[w.x]][w.y].iters);
+            int nh = 0;
+            for (const int2& w : wh) nh += hs[jg[w.x]][w.y].iters >= 0.6 * itmax ? 1 : 0;
+            g->nheavy[c128 ? 0 : 1] = std::min<int>(nh, (int)wh.size() / 8);
             VIE_CK(cudaMemcpyAsync(c128 ? g->work128 : g->work64, wh.data(), wh.size() * sizeof(int2),
                                    cudaMemcpyHostToDevice, s));
         }
@@ -668,7 +690,12 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             for (auto& st : hs) maxit_seen = std::max(maxit_seen, (int)std::ceil(st.iters));
         }
         g->tune_score[pi][tried] = ms / maxit_seen;
-        if (++g->tune_count[pi] == 2) g->tune_best[pi] = g->tune_score[pi][1] < g->tune_score[pi][0] ? kCand[1] : kCand[0];
+        if (++g->tune_count[pi] == 3) {
+            int best = 0;
+            for (int k = 1; k < 3; ++k)
+                if (g->tune_score[pi][k] < g->tune_score[pi][best]) best = k;
+            g->tune_best[pi] = kCand[best];
+        }
     }
     return VIE_OK;
 }

@@ -856,7 +856,7 @@ bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force) {
 
 template <class C>
 int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, int nwork, void* d_groups,
-                     int* d_next, double tol, int maxit, cudaStream_t s, int cluster) {
+                     int* d_next, double tol, int maxit, cudaStream_t s, int cluster, const InnerSplit* split) {
     if (jobs.empty() || nwork == 0) return VIE_OK;
     Twiddles tw;
     VIE_TRY(get_twiddles(&tw));
@@ -900,44 +900,61 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
     }
     VIE_TRY(reg_twiddles_ready(tw));   // constant-memory twiddles of the register path
     VIE_CK(cudaMemcpyAsync(d_groups, hg.data(), hg.size() * sizeof(InnerGroup<C>), cudaMemcpyHostToDevice, s));
-    VIE_CK(cudaMemsetAsync(d_next, 0, sizeof(int), s));
+    const bool two = split != nullptr && split->nheavy > 0 && split->nheavy < nwork && !inner_cluster_forced();
+    VIE_CK(cudaMemsetAsync(d_next, 0, (two ? 2 : 1) * sizeof(int), s));
     // opt in to the exact dynamic size: the default 48 KB limit also counts the static shared memory
     VIE_CK(cudaFuncSetAttribute(k_inner<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // one block per cluster of R CTAs; as many clusters as fit at once, pulling blocks from the queue
+    auto launch = [&](const int2* work, int n, int* next, int R, cudaStream_t st, int* units) -> int {
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = R;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(R);
+        cfg.blockDim = dim3(kInnerThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        VIE_CK(cudaOccupancyMaxActiveClusters(&nclusters, k_inner<C>, &cfg));
+        cfg.gridDim = dim3(std::max(1, std::min(n, nclusters)) * R);
+        cudaError_t le = cudaLaunchKernelEx(&cfg, k_inner<C>, reinterpret_cast<const InnerGroup<C>*>(d_groups), work,
+                                            n, next, tol, maxit, tw_of<C>(tw), units);
+        if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchKernelEx(k_inner)", __FILE__, __LINE__);
+        return VIE_OK;
+    };
     const int R = inner_cluster_forced() ? inner_cluster_forced() : (cluster > 0 ? cluster : 2);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = R;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(R);
-    cfg.blockDim = dim3(kInnerThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    VIE_CK(cudaOccupancyMaxActiveClusters(&nclusters, k_inner<C>, &cfg));
-    cfg.gridDim = dim3(std::max(1, std::min(nwork, nclusters)) * R);
-    // the kernel adds the KB it moves (per MVM) to its profiling counter
     (void)bytes_per_block;
+    // the kernels add the KB they move (per MVM) to one profiling counter; the profiled interval
+    // covers both parts of a split launch
     int* units = prof_begin(s, PK_INNER, sizeof(C) == 16 ? VIE_C128 : VIE_C64, 1024, 0, true);
-    cudaError_t le = cudaLaunchKernelEx(&cfg, k_inner<C>, reinterpret_cast<const InnerGroup<C>*>(d_groups), d_work,
-                                        nwork, d_next, tol, maxit, tw_of<C>(tw), units);
-    if (le != cudaSuccess) {
-        prof_end(s);
-        return cuda_fail(le, "cudaLaunchKernelEx(k_inner)", __FILE__, __LINE__);
+    int rc = VIE_OK;
+    if (!two) {
+        rc = launch(d_work, nwork, d_next, R, s, units);
+    } else {
+        // the heavy part first, so its clusters are resident before the light part fills the GPU
+        cudaError_t e = cudaEventRecord(split->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(split->s2, split->fork, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "split launch fork", __FILE__, __LINE__);
+        if (!rc) rc = launch(d_work, split->nheavy, d_next, split->cluster, s, units);
+        if (!rc) rc = launch(d_work + split->nheavy, nwork - split->nheavy, d_next + 1, R, split->s2, units);
+        e = cudaEventRecord(split->join, split->s2);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, split->join, 0);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "split launch join", __FILE__, __LINE__);
     }
     prof_end(s);
+    if (rc) return rc;
     VIE_CK(cudaGetLastError());
     return VIE_OK;
 }
 
 template int inner_persistent<double2>(const std::vector<InnerJob<double2>>&, const int2*, int, void*, int*, double,
-                                       int, cudaStream_t, int);
+                                       int, cudaStream_t, int, const InnerSplit*);
 template int inner_persistent<float2>(const std::vector<InnerJob<float2>>&, const int2*, int, void*, int*, double, int,
-                                      cudaStream_t, int);
+                                      cudaStream_t, int, const InnerSplit*);
 
 size_t inner_group_desc_bytes() { return std::max(sizeof(InnerGroup<double2>), sizeof(InnerGroup<float2>)); }
 

@@ -217,12 +217,15 @@ struct vie_grid {
     std::vector<int2> work_host[2];
     std::vector<int> job_group[2];
     void* inner_groups = nullptr;         // device copy of the per-group descriptors
-    int* inner_next = nullptr;            // work counter
+    int* inner_next = nullptr;            // work counters [2] (second: the split launch's light part)
+    cudaStream_t s2 = nullptr;            // stream of the light part of a split block-solver launch
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // cluster-size autotuning of the persistent solver, per precision (0: c128, 1: c64):
     // applies 0 and 1 try the candidates, later applies use the best
     int tune_count[2] = {0, 0};
     int tune_best[2] = {0, 0};
-    double tune_score[2][2] = {{0, 0}, {0, 0}};
+    double tune_score[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int nheavy[2] = {0, 0};               // blocks of the split launch's heavy part (from the last apply)
     cudaEvent_t tev[2] = {nullptr, nullptr};
     int64_t device_bytes = 0;
     std::vector<void*> allocations;
@@ -306,10 +309,20 @@ template <class C> struct InnerJob {
 };
 bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force);
 size_t inner_group_desc_bytes();
-// cluster: CTAs per block (1, 2, 4, 8; 0 = 2), unless VIE_INNER_CLUSTER forces one
+// cluster: CTAs per block (1, 2, 4, 8; 0 = 2), unless VIE_INNER_CLUSTER forces one.
+// Split launch (split != null, 0 < split->nheavy < nwork): the first nheavy work items run
+// with split->cluster CTAs per block on s while the rest run with `cluster` CTAs per block on
+// split->s2, concurrently; d_next must hold two counters; s waits for both.
+struct InnerSplit {
+    int nheavy = 0;
+    int cluster = 4;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
 template <class C>
 int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, int nwork, void* d_groups,
-                     int* d_next, double tol, int maxit, cudaStream_t s, int cluster = 0);
+                     int* d_next, double tol, int maxit, cudaStream_t s, int cluster = 0,
+                     const InnerSplit* split = nullptr);
 int inner_cluster_forced();
 template <class C> inline const C* tw_of(const Twiddles& t);
 template <> inline const double2* tw_of<double2>(const Twiddles& t) { return t.d128; }
