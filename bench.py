@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--serve-sizes", default="32,64", help="cubic grid sizes of the serving stream")
     ap.add_argument("--serve-kinds", default="metasurface",
                     help="structures of the serving stream: metasurface and/or solar_cell (comma separated)")
+    ap.add_argument("--serve-sweep", default="",
+                    help="comma-separated fractions of the measured saturation rate for a latency sweep (off by default)")
+    ap.add_argument("--serve-sweep-requests", type=int, default=24, help="requests per sweep point")
     ap.add_argument("--batch", type=int, default=64, help="instances in the batched-solve run (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -385,35 +388,55 @@ def main():
 
     # serving: Poisson arrivals, continuous batching over slots (p50/p99 latency)
     serving = None
-    if args.serve > 0:
+    serving_sweep = None
+    if args.serve > 0 or args.serve_sweep:
         from paper_2501_13512_gb300 import serve
         sizes = tuple(int(v) for v in args.serve_sizes.split(","))
         wts = [serve.SIZE_WEIGHTS[serve.SIZES.index(n)] if n in serve.SIZES else 1.0 for n in sizes]
         kinds = tuple(args.serve_kinds.split(","))
-        reqs = serve.make_stream(args.serve, seed=rank, sizes=sizes, weights=wts, kinds=kinds, outer_maxit=400)
-        for r in reqs:
-            r.want_field = False
-        srv = serve.Server(budget_bytes=int(0.5 * torch.cuda.get_device_properties(0).total_memory), slots=4)
-        rng = np.random.default_rng(1 + rank)
-        futs = []
-        t0 = time.perf_counter()
-        try:
+        workload = (f"{'/'.join(kinds)} structures on n^3 grids (n in {list(sizes)}), h = 10 nm, wavelengths "
+                    "400-800 nm (10 nm grid), random incidence; mixed, outer 1e-6, inner 1e-2, outer_maxit 400")
+        budget = int(0.5 * torch.cuda.get_device_properties(0).total_memory)
+
+        def serve_run(nreq, rate, seed):
+            """One request stream through a fresh server; rate None = all requests at once."""
+            reqs = serve.make_stream(nreq, seed=seed, sizes=sizes, weights=wts, kinds=kinds, outer_maxit=400)
             for r in reqs:
-                futs.append(srv.submit(r))
-                time.sleep(rng.exponential(1.0 / args.serve_rate))
-            res = [f.result(timeout=600) for f in futs]
-        finally:
-            srv.close()
-        slat = np.array([x.latency_s for x in res])
-        st = srv.latency_stats()
-        serving = {"requests": len(res), "arrival_rate": args.serve_rate, "sizes": list(sizes), "slots": 4,
-                   "p50_s": float(np.percentile(slat, 50)), "p99_s": float(np.percentile(slat, 99)),
-                   "solves_per_s": st["solves_per_s"],
-                   "converged": int(sum(x.stats["status"] == 0 for x in res)),
-                   "max_true_rel_res": float(max(x.stats["true_rel_res"] for x in res)),
-                   "cache": dict(srv.engine.hits),
-                   "workload": f"{'/'.join(kinds)} structures on n^3 grids, h = 10 nm, wavelengths 400-800 nm "
-                               "(10 nm grid), random incidence; mixed, outer 1e-6, inner 1e-2, outer_maxit 400"}
+                r.want_field = False
+            srv = serve.Server(budget_bytes=budget, slots=4)
+            rng = np.random.default_rng(1 + seed)
+            futs = []
+            try:
+                for r in reqs:
+                    futs.append(srv.submit(r))
+                    if rate:
+                        time.sleep(rng.exponential(1.0 / rate))
+                res = [f.result(timeout=600) for f in futs]
+            finally:
+                srv.close()
+            slat = np.array([x.latency_s for x in res])
+            st = srv.latency_stats()
+            return {"requests": len(res), "arrival_rate": rate, "sizes": list(sizes), "slots": 4,
+                    "p50_s": float(np.percentile(slat, 50)), "p99_s": float(np.percentile(slat, 99)),
+                    "solves_per_s": st["solves_per_s"],
+                    "converged": int(sum(x.stats["status"] == 0 for x in res)),
+                    "max_true_rel_res": float(max(x.stats["true_rel_res"] for x in res)),
+                    "cache": dict(srv.engine.hits)}
+
+        if args.serve > 0:
+            serving = serve_run(args.serve, args.serve_rate, rank)
+            serving["workload"] = workload
+        if args.serve_sweep:
+            # saturation: every request submitted at once; then Poisson streams at fractions of it
+            n = args.serve_sweep_requests
+            sat = serve_run(n, None, 100 + rank)
+            rows = []
+            for f in (float(v) for v in args.serve_sweep.split(",")):
+                r = serve_run(n, f * sat["solves_per_s"], 200 + rank)
+                r["fraction_of_saturation"] = f
+                rows.append(r)
+            serving_sweep = {"saturation_solves_per_s": sat["solves_per_s"], "saturation": sat, "rates": rows,
+                             "workload": workload}
 
     # batched independent solves: blob instances of several sizes, one persistent launch per size
     batched = None
@@ -466,6 +489,8 @@ def main():
             "plain_c128": plain, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "roofline_full_grid_mvm": roof_mvm, "kernels": kernels, "clocks": clocks,
             "serving": serving, "batched": batched, "cpu_baseline": cpu}
+    if serving_sweep is not None:
+        line["serving_sweep"] = serving_sweep
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

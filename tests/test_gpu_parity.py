@@ -266,3 +266,27 @@ def test_solve_rejects_overlapping_x0():
     o = vie.SolveOpts(1e-6, 1e-2, 10, 10, 1, vie.MODE_MIXED, 0, 0.0, b.data_ptr())
     st = vie.SolveStats()
     assert lib.vie_solve(g.handle, sp.handle, b.data_ptr(), e.data_ptr(), o, None, st) == vie.VIE_EINVAL
+
+
+def test_precond_every_tuner_candidate_meets_inner_tolerance():
+    # the first three applies of a persistent grid run the cluster-size candidates (2 CTAs per block,
+    # 4 CTAs, and the split launch: slowest blocks on 4, the rest on 2 on a second stream), the
+    # fourth the chosen one; every block of every apply meets the inner tolerance
+    w = inputs.metasurface(cells=4, seed=3)
+    rng = np.random.default_rng(8)
+    b = rng.normal(size=(3,) + w.eps_r.shape) + 1j * rng.normal(size=(3,) + w.eps_r.shape)
+    g = vie.Grid.from_workload(w, inner=vie.INNER_PERSISTENT)
+    sp = g.spectrum(w.k0)
+    bb = b.astype(np.complex64).astype(np.complex128)
+    blocks = oprecond.find_blocks(w.block_id)
+    ops = [omvm.FFTOperator(w.eps_r[blk.slices], w.h, w.k0, mask=blk.mask) for blk in blocks]
+    for apply in range(4):
+        y, st = g.precond(sp, dev(b, torch.complex64), inner_tol=1e-2)
+        assert st["nblocks"] == 16 and st["not_converged"] == 0 and st["breakdowns"] == 0
+        y = host(y)
+        for blk, op in zip(blocks, ops):
+            sl = (slice(None),) + blk.slices
+            bk = np.where(blk.mask[None], bb[sl], 0)
+            xk = np.where(blk.mask[None], y[sl], 0)
+            assert np.linalg.norm(bk - op(xk)) <= 1.01e-2 * np.linalg.norm(bk), (apply, blk.slices)
+    assert g.info()["inner_cluster"][1] in (2, 4, -1)
