@@ -440,14 +440,18 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
         // frequency f and the position pm of -f (mirror pairs; the smaller position does the work)
         const int cst = LZ * kZCols;
         constexpr int LGZ = ILog2<LZ>::v;
-        for (int task = t; task < LZ * nc; task += T) {
-            const int i = task >> lnc, c = task & (nc - 1);
-            const int f = LGZ ? (int)(__brev((unsigned)i) >> (32 - LGZ)) : 0;
-            const int fm = (LZ - f) & (LZ - 1);
-            const int im = LGZ ? (int)(__brev((unsigned)fm) >> (32 - LGZ)) : 0;
-            if (im < i) continue;
-            const F* gp = g.G + i * P + c0 + c;
-            const F gxx = gp[0], gxy = gp[gc], gxz = gp[2 * gc], gyy = gp[3 * gc], gyz = gp[4 * gc], gzz = gp[5 * gc];
+        // tasks = (frequency f in [0, LZ/2], column): exactly the working mirror pairs; two tasks per
+        // step with all twelve spectrum loads issued before either multiply
+        const int nwork = (LZ / 2 + 1) * nc;
+        auto pair_of = [&](int task, int& i, int& im, int& c) {
+            const int f = task >> lnc;
+            c = task & (nc - 1);
+            const int i1 = LGZ ? (int)(__brev((unsigned)f) >> (32 - LGZ)) : 0;
+            const int i2 = LGZ ? (int)(__brev((unsigned)((LZ - f) & (LZ - 1))) >> (32 - LGZ)) : 0;
+            i = min(i1, i2);
+            im = max(i1, i2);
+        };
+        auto apply = [&](int i, int im, int c, F gxx, F gxy, F gxz, F gyy, F gyz, F gzz) {
             {
                 F* q = sm + i * kZCols + c;
                 F X = q[0], Y = q[cst], Z = q[2 * cst];
@@ -462,6 +466,18 @@ __device__ __forceinline__ void z_reg(const InnerGroup<F>& g, F* W2, F* sm, cons
                 q[cst] = cmul(gxy, X) + cmul(gyy, Y) - cmul(gyz, Z);
                 q[2 * cst] = cmul(gzz, Z) - cmul(gxz, X) - cmul(gyz, Y);
             }
+        };
+        for (int task = t; task < nwork; task += 2 * T) {
+            int i0, im0, c0_, i1, im1, c1_;
+            pair_of(task, i0, im0, c0_);
+            const bool two = task + T < nwork;
+            pair_of(two ? task + T : task, i1, im1, c1_);
+            const F* gp0 = g.G + i0 * P + c0 + c0_;
+            const F* gp1 = g.G + i1 * P + c0 + c1_;
+            const F a0 = gp0[0], a1 = gp0[gc], a2 = gp0[2 * gc], a3 = gp0[3 * gc], a4 = gp0[4 * gc], a5 = gp0[5 * gc];
+            const F b0 = gp1[0], b1 = gp1[gc], b2 = gp1[2 * gc], b3 = gp1[3 * gc], b4 = gp1[4 * gc], b5 = gp1[5 * gc];
+            apply(i0, im0, c0_, a0, a1, a2, a3, a4, a5);
+            if (two) apply(i1, im1, c1_, b0, b1, b2, b3, b4, b5);
         }
         __syncthreads();
         for (int task = t; task < 3 * nc; task += T) {
