@@ -109,10 +109,19 @@ class OracleSample:
 
 
 def outer_iters_reference(default):
+    """Outer-iteration count that scales the oracle's per-iteration time to a full solve: the oracle's
+    own full solve when recorded, else `default` (the GPU solve of this run), else the count of the
+    committed bench line."""
     if os.path.exists(GOLDEN):
         with open(GOLDEN) as f:
             return float(json.load(f)["outer_iters"]), "oracle full solve (tests/golden/metasurface_reference.json)"
-    return float(default), "GPU mixed solve of the same workload (oracle full-solve count not yet recorded)"
+    if default is not None:
+        return float(default), "GPU mixed solve of the same workload (oracle full-solve count not yet recorded)"
+    rec = os.path.join(ROOT, "profiles", "bench_metasurface_256x256x16.json")
+    with open(rec) as f:
+        n = float(json.load(f)["solve"]["outer_iters"])
+    return n, ("GPU mixed solve of the committed bench line (profiles/bench_metasurface_256x256x16.json; "
+               "oracle full-solve count not yet recorded)")
 
 
 def run_reference(args, rank):
@@ -121,7 +130,7 @@ def run_reference(args, rank):
         return
     from paper_2501_13512_gb300 import inputs
     w = inputs.metasurface()
-    iters, src = outer_iters_reference(20.0)
+    iters, src = outer_iters_reference(None)
     times = []
     sample = ""
     smp = OracleSample(w, block_stride=16)
