@@ -4,6 +4,8 @@ import os
 import re
 import subprocess
 
+import numpy as np
+
 from paper_2501_13512_gb300 import build, vie
 
 
@@ -58,3 +60,25 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(pyname, "size")] == ctypes.sizeof(cls), pyname
         for field, _ in cls._fields_:
             assert got[(pyname, field)] == getattr(cls, field).offset, (pyname, field)
+
+
+def test_argument_validation_without_gpu():
+    # limits and malformed arguments are rejected before any CUDA call, with a message
+    lib = vie.load()
+    eps = np.ones(2 * 4, dtype=np.float64)
+    for dims, h in (((513, 1, 1), 1.0), ((0, 4, 1), 1.0), ((2, 2, 1), 0.0), ((2, 2, 1), float("nan"))):
+        d = vie.GridDesc(dims[0], dims[1], dims[2], h, eps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, 0)
+        out = ctypes.c_void_p()
+        assert lib.vie_grid_create(ctypes.byref(d), ctypes.byref(out)) == vie.VIE_EINVAL, (dims, h)
+        assert out.value is None
+        assert vie.last_error()
+    d = vie.GridDesc(2, 2, 1, 1.0, eps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, 7)
+    assert lib.vie_grid_create(ctypes.byref(d), ctypes.byref(ctypes.c_void_p())) == vie.VIE_EINVAL
+    for count in (0, 21846):
+        b = vie.BatchDesc(2, 2, 1, 1.0, count, eps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+        assert lib.vie_batch_create(ctypes.byref(b), ctypes.byref(ctypes.c_void_p())) == vie.VIE_EINVAL
+    # the no-allocation MVM: padded volume above 32768 points (17^3 pads to 64^3), null pointers
+    buf = ctypes.c_void_p(16)
+    assert lib.vie_matvec_noalloc(17, 17, 17, 1.0, 1.0, buf, buf, buf, None) == vie.VIE_EINVAL
+    assert "exceeds" in vie.last_error()
+    assert lib.vie_matvec_noalloc(4, 4, 4, 1.0, 1.0, None, buf, buf, None) == vie.VIE_EINVAL
