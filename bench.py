@@ -340,6 +340,17 @@ def main():
         accuracy = {"sampled_rel_field_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
                     "oracle_outer_iters": gd["outer_iters"], "samples": len(ref)}
 
+    # far-field post-processing of the solved field: bistatic RCS over a 361-direction sweep (E-plane)
+    th = np.linspace(0.0, 2.0 * np.pi, 361)
+    dirs = np.stack([np.sin(th), np.zeros_like(th), np.cos(th)], 1)
+    g.far_field_rcs(w.k0, e_mixed, dirs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.far_field_rcs(w.k0, e_mixed, dirs)
+    t_ff = time.perf_counter() - t0
+    far_field = {"directions": len(th), "ms": t_ff * 1e3, "directions_per_s": len(th) / t_ff,
+                 "note": "vie_far_field_rcs on the solved metasurface field, FP64, host-timed incl. read-back"}
+
     # end to end through the host-buffer API: pinned E_inc in, E out, copies inside the timed region
     e2e = None
     if args.e2e_steps > 0:
@@ -495,7 +506,7 @@ def main():
                       "precond_applies": last["precond_applies"], "matvecs_c128": last["matvecs_c128"],
                       "matvecs_c64": last["matvecs_c64"], "refinements": last["refinements"],
                       "true_rel_res": last["true_rel_res"]},
-            "plain_c128": plain, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches,
+            "plain_c128": plain, "accuracy": accuracy, "far_field": far_field, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "roofline_full_grid_mvm": roof_mvm, "kernels": kernels, "clocks": clocks,
             "serving": serving, "batched": batched, "cpu_baseline": cpu}
     if serving_sweep is not None:

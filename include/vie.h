@@ -251,6 +251,22 @@ int vie_batch_solve(vie_batch* batch, const double* k0s, const void* einc_dev,
                     void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
                     vie_solve_stats* stats);
 
+/* Bistatic radar cross section of a solved field (the far-zone limit of the
+ * scattered field of Eq. 1 with J = j w eps0 chi E; Section III's RCS
+ * comparisons, Figs. 1-2): for each direction u,
+ *   P(u) = sum_j chi_j E_j h^3 exp(j k0 u . r_j),
+ *   rcs[i] = k0^4 / (4 pi) |(I - u u) P(u)|^2,
+ * with voxel centres r_j = ((i + 1/2) h - n h / 2) per axis (the grid's centre
+ * at the origin) and chi = eps_r - 1 of the grid. e_dev: DEVICE complex128
+ * [3][nz][ny][nx] (e.g. the output of vie_solve). dirs_host: HOST ndir x 3 unit
+ * vectors (|u| = 1 within 1e-9, else VIE_EINVAL). rcs_host: HOST ndir doubles,
+ * written before return (the call synchronises `stream`). FP64 throughout.
+ * Returns VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA. No paper counterpart for
+ * the interface; the quantity is the paper's validation metric. */
+int vie_far_field_rcs(const vie_grid* grid, double k0, const void* e_dev,
+                      int32_t ndir, const double* dirs_host, double* rcs_host,
+                      vie_stream_t stream);
+
 /* Device bytes held by the batch (with its cached spectra), and whether its
  * corrections run in the persistent kernel (1) or in batched launches (0). */
 int vie_batch_get_info(const vie_batch* batch, int64_t* device_bytes, int32_t* persistent);

@@ -12,7 +12,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["fft.cu", "krylov.cu", "fields.cu", "api.cu", "profile.cu", "inner.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["fft.cu", "krylov.cu", "fields.cu", "api.cu", "profile.cu", "inner.cu", "noalloc.cu", "batch.cu",
+           "farfield.cu"]
 HEADERS = [os.path.join(CSRC, "vie_internal.cuh"), os.path.join(CSRC, "fft_core.cuh"), os.path.join(CSRC, "fft_reg.cuh"),
            os.path.join(ROOT, "include", "vie.h")]
 LIB = os.path.join(HERE, "libvie.so")

@@ -105,6 +105,7 @@ def load(path=LIB_PATH):
         "vie_block_precond_apply": ([P, P, c_int, P, P, c_double, c_int, P, POINTER(PrecondStats)], c_int),
         "vie_solve": ([P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
         "vie_matvec_noalloc": ([c_int32, c_int32, c_int32, c_double, c_double, P, P, P, P], c_int),
+        "vie_far_field_rcs": ([P, c_double, P, c_int32, POINTER(c_double), POINTER(c_double), P], c_int),
         "vie_batch_create": ([POINTER(BatchDesc), POINTER(P)], c_int),
         "vie_batch_destroy": ([P], c_int),
         "vie_batch_solve": ([P, POINTER(c_double), P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
@@ -284,6 +285,15 @@ class Grid:
         if check:
             _check(rc, allow=(VIE_ENOTCONV,))
         return e, _struct_dict(st)
+
+    def far_field_rcs(self, k0, e, dirs):
+        """Bistatic RCS of the field e (complex128 CUDA tensor) in the unit directions dirs (n x 3)."""
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
+        out = np.empty(d.shape[0], dtype=np.float64)
+        _check(load().vie_far_field_rcs(self.handle, float(k0), self._vec(e, C128, "e"), d.shape[0],
+                                        d.ctypes.data_as(POINTER(c_double)), out.ctypes.data_as(POINTER(c_double)),
+                                        _stream()))
+        return out
 
     def solve_host(self, spec, einc_host, out_host, **kw):
         """End-to-end solve from pinned host memory: H2D copy, solve, D2H copy."""
