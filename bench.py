@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--serve-sweep", default="",
                     help="comma-separated fractions of the measured saturation rate for a latency sweep (off by default)")
     ap.add_argument("--serve-sweep-requests", type=int, default=24, help="requests per sweep point")
+    ap.add_argument("--block-sweep", default="",
+                    help="comma-separated metasurface block divisions for a Table 2 style sweep: 0 = one block per "
+                         "pillar, m > 0 = m x m unit cells per block, air included (off by default)")
     ap.add_argument("--batch", type=int, default=64, help="instances in the batched-solve run (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -458,6 +461,29 @@ def main():
             serving_sweep = {"saturation_solves_per_s": sat["solves_per_s"], "saturation": sat, "rates": rows,
                              "workload": workload}
 
+    # block-division sweep (Table 2's trade-off): blocks vs outer iterations vs time, one solve each
+    block_sweep = None
+    if args.block_sweep:
+        block_sweep = []
+        for m in (int(v) for v in args.block_sweep.split(",")):
+            wb = inputs.metasurface(block_cells=m)
+            gb = vie.Grid.from_workload(wb)
+            spb = gb.spectrum(wb.k0)
+            eb = gb.plane_wave(wb.k0, wb.khat, wb.pol)
+            gb.solve(spb, eb, outer_tol=wb.outer_tol, inner_tol=wb.inner_tol, mode=vie.MODE_MIXED, outer_maxit=20,
+                     max_refinements=1, check=False)          # warm-up: tuner and first-use costs
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, stb = gb.solve(spb, eb, outer_tol=wb.outer_tol, inner_tol=wb.inner_tol, mode=vie.MODE_MIXED,
+                              check=False)
+            torch.cuda.synchronize()
+            block_sweep.append({"division": "pillar" if m == 0 else f"{m}x{m} cells", "blocks": gb.info()["nblocks"],
+                                "s": time.perf_counter() - t0, "outer_iters": stb["outer_iters"],
+                                "inner_iters": stb["inner_iters"], "precond_applies": stb["precond_applies"],
+                                "true_rel_res": stb["true_rel_res"], "status": stb["status"],
+                                "inner_cluster": gb.info()["inner_cluster"][1]})
+            gb.close()
+
     # batched independent solves: blob instances of several sizes, one persistent launch per size
     batched = None
     if args.batch > 0:
@@ -511,6 +537,8 @@ def main():
             "serving": serving, "batched": batched, "cpu_baseline": cpu}
     if serving_sweep is not None:
         line["serving_sweep"] = serving_sweep
+    if block_sweep is not None:
+        line["block_sweep"] = block_sweep
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -86,12 +86,15 @@ def sphere_radius_voxels(n, radius, eps, h, lambda0=1.0):
 
 
 def metasurface(cells=16, period=16, nz=16, eps=6.25, seed=0, voxels_per_wl=20,
-                lambda0=1.0, focus=False, focal_wl=10.0):
+                lambda0=1.0, focus=False, focal_wl=10.0, block_cells=0):
     """Array of cylindrical pillars, one preconditioner block per pillar.
 
     The radius of pillar (a, b) is drawn from U[0.15, 0.4] * period (seeded).
     With focus=True it follows the hyperbolic focusing profile of Eq. 12
     instead: Phi = k (sqrt(x^2 + y^2 + d^2) - d), r = P (0.15 + 0.25 frac(Phi/2pi)).
+    block_cells = m > 0 instead makes every m x m group of unit cells one block,
+    air voxels included (the unit-cell division of Section III.A and the coarser
+    divisions of Table 2's trade-off).
     """
     h = lambda0 / voxels_per_wl
     nx = ny = cells * period
@@ -116,6 +119,12 @@ def metasurface(cells=16, period=16, nz=16, eps=6.25, seed=0, voxels_per_wl=20,
             xs = slice(b * period, (b + 1) * period)
             eps_r[:, ys, xs][:, disk] = eps
             bid[:, ys, xs][:, disk] = a * cells + b
+    if block_cells > 0:
+        m = int(block_cells)
+        cy = np.arange(ny) // (period * m)
+        cx = np.arange(nx) // (period * m)
+        nbx = (cells + m - 1) // m
+        bid = np.broadcast_to((cy[:, None] * nbx + cx[None, :]).astype(np.int32), (nz, ny, nx)).copy()
     return Workload("metasurface", (nx, ny, nz), h, lambda0, eps_r, bid,
                     inner_tol=1e-2, outer_tol=1e-6, use_precond=True)
 
