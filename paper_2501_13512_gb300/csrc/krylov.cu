@@ -139,7 +139,6 @@ __device__ void finalize(SegState& s, double2 d1, double2 d2, int* n_active, dou
 // One fused pass over a segment: vector update and/or up to two inner products.
 template <class C, int OP>
 __global__ void __launch_bounds__(kRedThreads) k_bicg(VecArgs<C> a) {
-    typedef typename real_of<C>::type R;
     const int seg = blockIdx.y;
     SegState& S = a.st[seg];
     if (OP != OP_INIT) {
@@ -190,7 +189,6 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg(VecArgs<C> a) {
             cdot_acc(acc2, t, t);
         }
     }
-    (void)sizeof(R);
     double2 d1 = Acc<C>::widen(acc1), d2 = Acc<C>::widen(acc2);
     block_sum2(d1, d2);
     __shared__ bool last;
