@@ -86,3 +86,57 @@ def kernel_components(DX, DY, DZ, h, k):
         diag = self_term(h, k) if p == q else 0.0
         out[name] = np.where(zero, diag, val)
     return out
+
+
+# ---------------------------------------------------------------- near-field variant
+# The paper does not say how near-neighbour couplings are integrated; the build's
+# primary reading samples K at the source voxel's centre (kernel_entry). The
+# variant below integrates k^2 G over the source voxel instead for offsets with
+# max |D| <= radius (D != 0): K(D) = int_{cube of side h centred at D h} k^2 G(r) d^3 r,
+# by tensor Gauss-Legendre quadrature. The integrand is smooth on those cubes
+# (the nearest point of the cube at D != 0 is at least h/2 from the origin).
+# Pinned by tests/test_oracle_near.py: convergence in q, an adaptive cubature of
+# scipy, the cube mean of a Helmholtz solution (f(c) (1 - (kh)^2 / 24) + O(h^4)),
+# parities and reciprocity.
+
+def k2G_at(rx, ry, rz, k):
+    """The six components of k^2 G(r) (Eq. 1) at arrays of points r != 0."""
+    R = np.sqrt(rx * rx + ry * ry + rz * rz)
+    g = scalar_green(R, k)
+    a = k * k - 1j * k / R - 1.0 / (R * R)
+    b = -k * k + 3j * k / R + 3.0 / (R * R)
+    u = (rx / R, ry / R, rz / R)
+    return {name: g * b * u[p] * u[q] + (g * a if p == q else 0.0) for name, (p, q) in PAIRS.items()}
+
+
+def cube_kernel(d, h, k, q):
+    """int over the cube of side h centred at d h of k^2 G, six components (d integer, != 0)."""
+    t, w = np.polynomial.legendre.leggauss(q)
+    x = (d[0] + 0.5 * t) * h
+    y = (d[1] + 0.5 * t) * h
+    z = (d[2] + 0.5 * t) * h
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :] / 8.0    # mean over the cube
+    vals = k2G_at(X, Y, Z, k)
+    return {name: h ** 3 * np.sum(W * v) for name, v in vals.items()}
+
+
+def kernel_components_near(DX, DY, DZ, h, k, radius, q):
+    """kernel_components with cube-integrated entries for 0 < max|D| <= radius."""
+    out = kernel_components(DX, DY, DZ, h, k)
+    DX = np.asarray(DX)
+    DY = np.asarray(DY)
+    DZ = np.asarray(DZ)
+    rng = range(-radius, radius + 1)
+    for dz in rng:
+        for dy in rng:
+            for dx in rng:
+                if dx == 0 and dy == 0 and dz == 0:
+                    continue
+                sel = (DX == dx) & (DY == dy) & (DZ == dz)
+                if not np.any(sel):
+                    continue
+                vals = cube_kernel((dx, dy, dz), h, k, q)
+                for name in COMPONENTS:
+                    out[name] = np.where(sel, vals[name], out[name])
+    return out

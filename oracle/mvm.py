@@ -14,7 +14,7 @@ covariance, Clausius-Mossotti for one voxel.
 """
 import numpy as np
 
-from .green import COMPONENTS, PAIRS, kernel_components
+from .green import COMPONENTS, PAIRS, kernel_components, kernel_components_near
 
 
 def component_name(a, b):
@@ -30,14 +30,21 @@ def voxel_index_coords(n):
     return X.ravel(), Y.ravel(), Z.ravel()
 
 
-def dense_G(n, h, k):
-    """The 3N x 3N matrix G with G[(a,i),(b,j)] = K_ab(p_i - p_j) (Eq. 4 discretised)."""
+def _components(DX, DY, DZ, h, k, near):
+    if near is None:
+        return kernel_components(DX, DY, DZ, h, k)
+    return kernel_components_near(DX, DY, DZ, h, k, near[0], near[1])
+
+
+def dense_G(n, h, k, near=None):
+    """The 3N x 3N matrix G with G[(a,i),(b,j)] = K_ab(p_i - p_j) (Eq. 4 discretised).
+    near = (radius, q): cube-integrated entries for 0 < max|D| <= radius (green.cube_kernel)."""
     X, Y, Z = voxel_index_coords(n)
     N = X.size
     DX = X[:, None] - X[None, :]
     DY = Y[:, None] - Y[None, :]
     DZ = Z[:, None] - Z[None, :]
-    K = kernel_components(DX, DY, DZ, h, k)
+    K = _components(DX, DY, DZ, h, k, near)
     G = np.zeros((3 * N, 3 * N), complex)
     for name, (p, q) in PAIRS.items():
         G[p * N:(p + 1) * N, q * N:(q + 1) * N] = K[name]
@@ -46,11 +53,11 @@ def dense_G(n, h, k):
     return G
 
 
-def dense_operator(eps_r, h, k):
+def dense_operator(eps_r, h, k, near=None):
     """A = I - G diag(chi) as a dense matrix (literal double sum of Eq. 4)."""
     nz, ny, nx = eps_r.shape
     chi = (eps_r - 1.0).ravel()
-    G = dense_G((nx, ny, nz), h, k)
+    G = dense_G((nx, ny, nz), h, k, near)
     D = np.tile(chi, 3)
     return np.eye(G.shape[0], dtype=complex) - G * D[None, :]
 
@@ -68,7 +75,7 @@ def wrapped_offsets(n_axis, M_axis):
     return d, used
 
 
-def kernel_array(n, M, h, k):
+def kernel_array(n, M, h, k, near=None):
     """The six components of K on the padded M grid, offsets wrapped circularly.
 
     Slot m along an axis holds offset m for m < n and m - M for m > M - n;
@@ -80,7 +87,7 @@ def kernel_array(n, M, h, k):
     dz, uz = wrapped_offsets(n[2], M[2])
     DZ, DY, DX = np.meshgrid(dz, dy, dx, indexing="ij")
     used = uz[:, None, None] & uy[None, :, None] & ux[None, None, :]
-    K = kernel_components(DX, DY, DZ, h, k)
+    K = _components(DX, DY, DZ, h, k, near)
     return {c: np.where(used, K[c], 0.0) for c in COMPONENTS}
 
 
@@ -92,7 +99,7 @@ class FFTOperator:
     acting on vectors supported on the subset.
     """
 
-    def __init__(self, eps_r, h, k, M=None, mask=None):
+    def __init__(self, eps_r, h, k, M=None, mask=None, near=None):
         nz, ny, nx = eps_r.shape
         self.n = (nx, ny, nz)
         self.M = tuple(M) if M is not None else default_padding(self.n)
@@ -101,7 +108,7 @@ class FFTOperator:
             chi = np.where(mask, chi, 0.0)
         self.chi = chi
         self.mask = mask
-        K = kernel_array(self.n, self.M, h, k)
+        K = kernel_array(self.n, self.M, h, k, near)
         s = (self.M[2], self.M[1], self.M[0])
         self.Khat = {c: np.fft.fftn(K[c], s=s, axes=(0, 1, 2)) for c in COMPONENTS}
 

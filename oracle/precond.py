@@ -51,11 +51,11 @@ def find_blocks(block_id):
 class BlockPreconditioner:
     """y = K2^{-1} b, each block solved inexactly by inner BiCGSTAB-FFT."""
 
-    def __init__(self, eps_r, block_id, h, k, inner_tol=1e-2, inner_maxit=1000):
+    def __init__(self, eps_r, block_id, h, k, inner_tol=1e-2, inner_maxit=1000, near=None):
         self.blocks = find_blocks(block_id)
         self.ops = []
         for b in self.blocks:
-            self.ops.append(FFTOperator(eps_r[b.slices], h, k, mask=b.mask))
+            self.ops.append(FFTOperator(eps_r[b.slices], h, k, mask=b.mask, near=near))
         self.inner_tol = inner_tol
         self.inner_maxit = inner_maxit
         self.last_inner_iters = []
