@@ -301,8 +301,8 @@ GOLDEN_MS = os.path.join(os.path.dirname(__file__), "golden", "metasurface_refer
 @pytest.mark.skipif(not os.path.exists(GOLDEN_MS), reason="oracle full-size reference not recorded")
 def test_metasurface_full_size_field_at_oracle_samples():
     # full 256x256x16 metasurface: the GPU field (mixed, solved to 1e-8) against the oracle's FP64
-    # block-preconditioned solve (1e-6) at 4096 seeded voxel samples. Both are solutions of the same
-    # system; the oracle's own error is at most kappa * 1e-6, so the comparison bound is loose.
+    # block-preconditioned solve (true residual 9.8e-7) at 4096 seeded voxel samples. Both solve the
+    # same system; the difference is the oracle's own error (measured 2.4e-6 with the GPU at 4.5e-7).
     gd = json.load(open(GOLDEN_MS))
     if not gd["true_rel_res"] <= 1.05e-6:
         pytest.skip(f"the oracle's reference solve stopped at true residual {gd['true_rel_res']:.2e}")
@@ -315,4 +315,4 @@ def test_metasurface_full_size_field_at_oracle_samples():
     idx = torch.tensor(gd["sample_index"], device="cuda")
     got = host(e.reshape(-1)[idx])
     ref = np.array(gd["sample_re"]) + 1j * np.array(gd["sample_im"])
-    assert rel(got, ref) <= 1e-3
+    assert rel(got, ref) <= 1e-4
