@@ -119,7 +119,10 @@ int vie_grid_get_info(const vie_grid* grid, vie_grid_info* info);
  * computes in FP64 on the device the 3D FFT of the six components of K for
  * the full grid and for every block group, at wavenumber k0 > 0.
  * precision_mask: VIE_C128, VIE_C64 or both (bitwise or); the complex64 copy
- * is rounded from the FP64 spectrum. The spectrum is owned by the caller and
+ * is rounded from the FP64 spectrum. Storage: the full-grid spectrum keeps
+ * (Mx/2+1)(My/2+1)(Mz/2+1) entries per component (each component is even or
+ * odd along every axis, so one octant of frequencies fixes it), block-group
+ * spectra the full Mx My Mz. The spectrum is owned by the caller and
  * serves the grid it was made for and every other grid with the same h, padded
  * shapes and block-group box extents (e.g. the same structure created twice);
  * it must be released before the grid it was made for is destroyed.
