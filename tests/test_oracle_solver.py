@@ -22,6 +22,32 @@ def test_bicgstab_matches_dense_solve():
     assert r <= 1e-10
 
 
+def test_bicgstab_initial_guess_matches_dense_solve():
+    # x0 branch: r0 = b - A x0, stopping test still relative to ||b|| (van der Vorst's algorithm from
+    # an arbitrary start); pinned against LU from three starts: a perturbed solution, a random vector,
+    # and the exact solution (no iteration at all)
+    eps_r, _, b = inputs.random_case((4, 3, 3), seed=23)
+    A = mvm.dense_operator(eps_r, H, K0)
+    xref = np.linalg.solve(A, b.ravel()).reshape(b.shape)
+    op = mvm.FFTOperator(eps_r, H, K0)
+    rng = np.random.default_rng(5)
+    kappa = np.linalg.cond(A)
+    noise = rng.normal(size=b.shape) + 1j * rng.normal(size=b.shape)
+    for x0 in (xref + 0.1 * noise, noise):
+        x0_copy = x0.copy()
+        x, info = krylov.bicgstab(op.apply, b, tol=1e-11, maxit=500, x0=x0)
+        assert info["status"] == krylov.CONVERGED
+        assert np.array_equal(x0, x0_copy)                # the start is not modified
+        assert np.linalg.norm(x - xref) <= 10 * kappa * 1e-11 * np.linalg.norm(xref)
+        assert np.linalg.norm(b.ravel() - A @ x.ravel()) <= 1e-10 * np.linalg.norm(b)
+    x, info = krylov.bicgstab(op.apply, b, tol=1e-9, maxit=500, x0=xref)
+    assert info["iters"] == 0 and info["matvecs"] == 1 and np.array_equal(x, xref)
+    # a start closer to the solution takes fewer iterations than a cold start to the same tolerance
+    _, cold = krylov.bicgstab(op.apply, b, tol=1e-8, maxit=500)
+    _, warm = krylov.bicgstab(op.apply, b, tol=1e-8, maxit=500, x0=xref + 1e-4 * noise)
+    assert warm["iters"] < cold["iters"]
+
+
 def test_bicgstab_zero_rhs_and_identity():
     b = np.zeros((3, 2, 2, 2), complex)
     x, info = krylov.bicgstab(lambda v: v, b, 1e-6, 10)
