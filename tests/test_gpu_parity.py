@@ -297,6 +297,40 @@ def test_precond_every_tuner_candidate_meets_inner_tolerance():
 
 GOLDEN_MS = os.path.join(os.path.dirname(__file__), "golden", "metasurface_reference.json")
 
+# Outer tolerance at which the solved field is within 1e-5 of the exact solution of the discretised
+# system (the oracle solved to 1e-10), in both modes, on the metasurface crops below.
+OUTER_TOL_FOR_1E5 = 1e-6
+
+
+def _crop_reference(cells):
+    p = os.path.join(os.path.dirname(__file__), "golden", f"metasurface_crop_{cells}x{cells}.npz")
+    if not os.path.exists(p):
+        pytest.skip(f"oracle reference {os.path.basename(p)} not recorded")
+    z = np.load(p)
+    return json.loads(str(z["meta"])), z["index"], z["value"]
+
+
+@pytest.mark.parametrize("cells", [4, 8])
+@pytest.mark.parametrize("mode", [vie.MODE_MIXED, vie.MODE_PLAIN_C128])
+def test_metasurface_crop_field_within_1e5_of_tight_oracle(cells, mode):
+    # 64x64x16 (4x4 pillars, every entry) and 128x128x16 (8x8 pillars, 65536 seeded entries): the
+    # block-preconditioned solve at outer tolerance 1e-6 against the oracle's solve to 1e-10, element
+    # by element over the stored entries (Section II.B; SURVEY's "several correct results" reading:
+    # iterates agree only within tolerance, so the reference is solved far tighter than the solve)
+    meta, idx, ref = _crop_reference(cells)
+    assert meta["true_rel_res"] <= 1e-10
+    w = inputs.metasurface(cells=cells, seed=0)
+    g = vie.Grid.from_workload(w)
+    sp = g.spectrum(w.k0)
+    e, st = g.solve(sp, g.plane_wave(w.k0, w.khat, w.pol), outer_tol=OUTER_TOL_FOR_1E5, inner_tol=w.inner_tol,
+                    mode=mode)
+    assert st["status"] == vie.VIE_OK and st["true_rel_res"] <= OUTER_TOL_FOR_1E5
+    got = host(e.reshape(-1)[torch.from_numpy(idx).cuda()])
+    err = rel(got, ref)
+    print(f"crop {cells}x{cells} mode {mode}: outer {st['outer_iters']} res {st['true_rel_res']:.2e} "
+          f"field err {err:.2e}")
+    assert err <= 1e-5
+
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN_MS), reason="oracle full-size reference not recorded")
 def test_metasurface_full_size_field_at_oracle_samples():
