@@ -49,7 +49,8 @@ enum vie_status {
     VIE_ENOTCONV = 4,    /* iteration limit reached; result and stats are valid */
     VIE_EBREAKDOWN = 5,  /* BiCGSTAB breakdown: rho, <rhat,v> or <t,t> is 0/NaN */
     VIE_ETIMEOUT = 6,    /* a bounded wait for the device gave up               */
-    VIE_EBUSY = 7        /* admission refused: not enough free device memory    */
+    VIE_EBUSY = 7        /* admission refused: the allocation would exceed the
+                            device budget of vie_set_device_budget              */
 };
 
 enum vie_precision {
@@ -70,12 +71,13 @@ typedef struct vie_spectrum vie_spectrum;
 typedef struct {
     int32_t nx, ny, nz;      /* voxels per axis, each in [1, 512]                    */
     double h;                /* voxel edge (same length unit as 2*pi/k0)             */
-    const double* eps_r;     /* HOST, 2*nx*ny*nz doubles: relative permittivity
-                                (re, im) per voxel, [nz][ny][nx]; copied             */
-    const int32_t* block_id; /* HOST, nx*ny*nz: subdomain of each voxel for the
-                                block-diagonal preconditioner, -1 = no block
-                                (identity); any non-negative ids; NULL = all -1;
-                                copied                                               */
+    const double* eps_r;     /* HOST or DEVICE, 2*nx*ny*nz doubles: relative
+                                permittivity (re, im) per voxel, [nz][ny][nx];
+                                copied (a device table is read back once)            */
+    const int32_t* block_id; /* HOST or DEVICE, nx*ny*nz: subdomain of each voxel
+                                for the block-diagonal preconditioner, -1 = no
+                                block (identity); any non-negative ids; NULL = all
+                                -1; copied                                           */
     uint32_t flags;          /* 0 or one VIE_GRID_INNER_* value                      */
 } vie_grid_desc;
 
@@ -104,8 +106,9 @@ typedef struct {
 
 /* Creates the grid on the current CUDA device: uploads chi = eps_r - 1,
  * partitions the blocks (Eq. 10) into groups that share a padded FFT shape,
- * and allocates all workspace. Errors: VIE_EINVAL (sizes, flags, nulls),
- * VIE_ENOMEM, VIE_ECUDA. */
+ * and allocates all workspace. Errors: VIE_EINVAL (sizes, flags, nulls,
+ * non-finite eps_r), VIE_EBUSY (the workspace would exceed the device budget;
+ * nothing is kept), VIE_ENOMEM, VIE_ECUDA. */
 int vie_grid_create(const vie_grid_desc* desc, vie_grid** out);
 
 /* Waits for the grid's device, then frees the grid and its workspace. Every
@@ -160,9 +163,12 @@ typedef struct {
  * system A_k x_k = b|S_k (rows/columns of A on the block's voxels, all three
  * components, Eq. 11) is solved by BiCGSTAB-FFT from x_k = 0 to
  * ||b_k - A_k x_k|| <= inner_tol ||b_k|| or inner_maxit iterations; y = b on
- * voxels of no block. All blocks of all groups are iterated together in
- * batched launches. b and y are vectors of `precision` and must not overlap.
- * stats may be NULL. Synchronous with the host at return. */
+ * voxels of no block. The blocks of the groups the persistent solver takes
+ * (vie_grid_flags) run in one persistent launch, each block solved to its own
+ * tolerance by one thread-block cluster; the other groups iterate in lockstep
+ * in batched launches, one per BiCGSTAB step. b and y are vectors of
+ * `precision` and must not overlap. stats may be NULL. Synchronous with the
+ * host at return. */
 int vie_block_precond_apply(vie_grid* grid, const vie_spectrum* spectrum,
                             int precision, const void* b_dev, void* y_dev,
                             double inner_tol, int inner_maxit,
@@ -313,10 +319,13 @@ int vie_profile_read(vie_kernel_stat* out, int cap, int* n_out, int64_t* total_l
  *       VIE_EINVAL with the limit in the message;
  *   h, k0: voxel edge and wavenumber (> 0);
  *   chi_dev: DEVICE, complex128 (re, im) chi = eps_r - 1, [nz][ny][nx];
- *   x_dev, y_dev: DEVICE, complex128 [3][nz][ny][nx], must not overlap.
+ *   x_dev, y_dev: DEVICE, complex128 [3][nz][ny][nx]; y must overlap
+ *       neither x nor chi (VIE_EINVAL).
  * The first call on a device, with that device current, resolves the array's
- * device address and writes its twiddle table (a synchronous host-to-device
- * copy); make that first call before any stream capture. Later calls only
+ * device address, writes its twiddle table (a synchronous host-to-device
+ * copy) and waits for the device (cudaDeviceSynchronize), so that a caller's
+ * non-blocking stream never reads the table early; make that first call
+ * before any stream capture. Later calls only
  * enqueue kernels on `stream`. All calls share the one array and overwrite
  * it: calls that overlap on the GPU (different streams, or different host
  * threads without ordering) race and give wrong results. Nothing in the array
@@ -324,6 +333,26 @@ int vie_profile_read(vie_kernel_stat* out, int cap, int* n_out, int64_t* total_l
 int vie_matvec_noalloc(int32_t nx, int32_t ny, int32_t nz, double h, double k0,
                        const double* chi_dev, const double* x_dev, double* y_dev,
                        vie_stream_t stream);
+
+/* Device memory budget for admission by footprint (a serving process that
+ * hosts several grids): every device allocation the library keeps for a grid,
+ * a spectrum or a batch is counted, process-wide, and a call whose allocation
+ * would take the count above `bytes` is refused with VIE_EBUSY and keeps
+ * nothing. 0 (the default) removes the budget. Transient temporaries inside a
+ * call (the FP64 spectrum source, far-field partial sums) are not counted.
+ * Lowering the budget below the bytes held refuses later allocations only.
+ * No paper counterpart. Errors: VIE_EINVAL (bytes < 0). */
+int vie_set_device_budget(int64_t bytes);
+
+/* Bytes the library's handles hold on the device now, and the budget (0 = none).
+ * Either pointer may be NULL. */
+int vie_device_usage(int64_t* held, int64_t* budget);
+
+/* Test hook for the out-of-memory paths: the counted allocation after the next
+ * `after` ones fails as if cudaMalloc had reported cudaErrorMemoryAllocation
+ * (VIE_ENOMEM), without calling it; -1 cancels. One failure per call of this
+ * function. No paper counterpart. */
+int vie_fault_inject_alloc(int32_t after);
 
 /* Copies the text of the last error on this thread into buf (NUL-terminated,
  * truncated to len). Returns the length of the full message. */

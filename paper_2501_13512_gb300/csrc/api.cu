@@ -60,22 +60,69 @@ int get_twiddles(Twiddles* out) {
     VIE_CK(cudaMalloc(&t.d64, kLmax * sizeof(float2)));
     VIE_CK(cudaMemcpy(t.d128, h128.data(), kLmax * sizeof(double2), cudaMemcpyHostToDevice));
     VIE_CK(cudaMemcpy(t.d64, h64.data(), kLmax * sizeof(float2), cudaMemcpyHostToDevice));
+    // copies from pageable memory may return before their DMA lands, and later kernels may run on a
+    // non-blocking stream that does not wait for the legacy stream: wait for the tables here
+    VIE_CK(cudaDeviceSynchronize());
     g_tw[dev] = t;
     *out = t;
     return VIE_OK;
 }
 
 // ---------------------------------------------------------------- allocation
+// Every device allocation a grid, spectrum or batch holds goes through dmalloc,
+// which counts the bytes held by the whole process against an optional budget.
+static std::mutex g_alloc_mu;
+static std::map<void*, size_t> g_alloc_size;
+static int64_t g_alloc_held = 0;
+static int64_t g_alloc_budget = 0;        // 0: no budget
+static int g_alloc_fault_after = -1;      // test hook: allocations left before an injected failure
+
+int dmalloc(void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) return VIE_OK;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    if (g_alloc_budget > 0 && g_alloc_held + (int64_t)bytes > g_alloc_budget)
+        return fail(VIE_EBUSY, std::string(what) + ": admission refused: " + std::to_string(bytes) +
+                                   " more bytes would exceed the device budget of " + std::to_string(g_alloc_budget) +
+                                   " (held " + std::to_string(g_alloc_held) + ")");
+    cudaError_t e;
+    if (g_alloc_fault_after == 0) {
+        g_alloc_fault_after = -1;
+        e = cudaErrorMemoryAllocation;          // injected: no device call is made
+    } else {
+        if (g_alloc_fault_after > 0) --g_alloc_fault_after;
+        e = cudaMalloc(p, bytes);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(VIE_ENOMEM, std::string(what) + ": cudaMalloc of " + std::to_string(bytes) +
+                                    " bytes failed: " + cudaGetErrorString(e));
+    }
+    g_alloc_size[*p] = bytes;
+    g_alloc_held += (int64_t)bytes;
+    return VIE_OK;
+}
+
+void dfree(void* p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        auto it = g_alloc_size.find(p);
+        if (it != g_alloc_size.end()) {
+            g_alloc_held -= (int64_t)it->second;
+            g_alloc_size.erase(it);
+        }
+    }
+    cudaFree(p);
+}
+
 template <class T>
 static int dalloc(vie_grid* g, T** p, int64_t count) {
     *p = nullptr;
     if (count <= 0) return VIE_OK;
     size_t bytes = (size_t)count * sizeof(T);
-    cudaError_t e = cudaMalloc((void**)p, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(VIE_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
-    }
+    VIE_TRY(dmalloc((void**)p, bytes, "vie_grid_create"));
     g->allocations.push_back((void*)*p);
     g->device_bytes += (int64_t)bytes;
     return VIE_OK;
@@ -156,7 +203,7 @@ static int upload_chi(vie_grid* g, BoxSet& bs, const std::vector<double2>& chi) 
 }
 
 static void release_grid(vie_grid* g) {
-    for (void* p : g->allocations) cudaFree(p);
+    for (void* p : g->allocations) dfree(p);
     g->allocations.clear();
     if (g->h_ring) cudaFreeHost(g->h_ring);
     for (int i = 0; i < 2; ++i) {
@@ -167,6 +214,17 @@ static void release_grid(vie_grid* g) {
     if (g->join_ev) cudaEventDestroy(g->join_ev);
     if (g->s2) cudaStreamDestroy(g->s2);
     delete g;
+}
+
+// True for memory the device owns (cudaMalloc, torch CUDA tensors); host,
+// pinned and managed memory are read in place.
+static bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice;
 }
 
 // Bounded host wait for an event (no device-side spin exists in this library;
@@ -190,6 +248,26 @@ static int wait_event(cudaEvent_t ev, double timeout_ms) {
 using namespace vie;
 
 extern "C" int vie_version(void) { return 100; }
+
+extern "C" int vie_set_device_budget(int64_t bytes) {
+    if (bytes < 0) return fail(VIE_EINVAL, "vie_set_device_budget: bytes must be >= 0");
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc_budget = bytes;
+    return VIE_OK;
+}
+
+extern "C" int vie_device_usage(int64_t* held, int64_t* budget) {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    if (held) *held = g_alloc_held;
+    if (budget) *budget = g_alloc_budget;
+    return VIE_OK;
+}
+
+extern "C" int vie_fault_inject_alloc(int32_t after) {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc_fault_after = after < 0 ? -1 : after;
+    return VIE_OK;
+}
 
 extern "C" int vie_last_error(char* buf, size_t len) {
     if (buf && len) {
@@ -216,10 +294,28 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
     const int64_t N = (int64_t)d->nx * d->ny * d->nz;
     g->N = N;
 
+    // eps_r and block_id may be host or device memory: device tables are read back once
+    std::vector<double> eps_host;
+    std::vector<int32_t> bid_host;
+    const double* eps = d->eps_r;
+    const int32_t* user_bid = d->block_id;
+    if (is_device_pointer(eps)) {
+        eps_host.resize(2 * N);
+        if (cudaMemcpy(eps_host.data(), eps, 2 * N * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(VIE_ECUDA, "vie_grid_create: reading the device eps_r failed"));
+        eps = eps_host.data();
+    }
+    if (user_bid && is_device_pointer(user_bid)) {
+        bid_host.resize(N);
+        if (cudaMemcpy(bid_host.data(), user_bid, N * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(VIE_ECUDA, "vie_grid_create: reading the device block_id failed"));
+        user_bid = bid_host.data();
+    }
+
     // contrast chi = eps_r - 1 (Eq. 2: J = j w eps0 chi E)
     std::vector<double2> chi(N);
     for (int64_t i = 0; i < N; ++i) {
-        double re = d->eps_r[2 * i], im = d->eps_r[2 * i + 1];
+        double re = eps[2 * i], im = eps[2 * i + 1];
         if (!std::isfinite(re) || !std::isfinite(im)) return bail(fail(VIE_EINVAL, "vie_grid_create: non-finite eps_r"));
         chi[i] = make_double2(re - 1.0, im);
     }
@@ -233,13 +329,13 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
     // blocks of Eq. 10: compact ids in increasing order of the user's ids
     std::vector<int32_t> bid(N, -1);
     std::map<int32_t, int> ids;
-    if (d->block_id) {
+    if (user_bid) {
         for (int64_t i = 0; i < N; ++i)
-            if (d->block_id[i] >= 0) ids.emplace(d->block_id[i], 0);
+            if (user_bid[i] >= 0) ids.emplace(user_bid[i], 0);
         int k = 0;
         for (auto& kv : ids) kv.second = k++;
         for (int64_t i = 0; i < N; ++i)
-            if (d->block_id[i] >= 0) bid[i] = ids[d->block_id[i]];
+            if (user_bid[i] >= 0) bid[i] = ids[user_bid[i]];
     }
     const int K = (int)ids.size();
     g->nblocks = K;
@@ -419,8 +515,10 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
     sp->k0 = k0;
     sp->precision_mask = mask;
     auto bail = [&](int rc) {
-        for (auto p : sp->g128) cudaFree(p);
-        for (auto p : sp->g64) cudaFree(p);
+        cudaStreamSynchronize(s);         // kernels already queued may still use the spectra
+        for (auto p : sp->g128) dfree(p);
+        for (auto p : sp->g64) dfree(p);
+        for (auto p : sp->go64) dfree(p);
         delete sp;
         return rc;
     };
@@ -432,14 +530,16 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
         const int64_t n = 6 * g->full.oct_elems();
         double2* G = nullptr;
         float2* G64 = nullptr;
-        if (((mask & VIE_C128) && cudaMalloc(&G, n * sizeof(double2)) != cudaSuccess) ||
-            ((mask & VIE_C64) && cudaMalloc(&G64, n * sizeof(float2)) != cudaSuccess)) {
-            cudaGetLastError();
-            if (G) cudaFree(G);
-            return bail(fail(VIE_ENOMEM, "spectrum allocation failed"));
+        int arc = VIE_OK;
+        if (mask & VIE_C128) arc = dmalloc((void**)&G, n * sizeof(double2), "vie_green_spectrum");
+        if (!arc && (mask & VIE_C64)) arc = dmalloc((void**)&G64, n * sizeof(float2), "vie_green_spectrum");
+        if (arc) {
+            dfree(G);
+            return bail(arc);
         }
         sp->g128.push_back(G);
         sp->g64.push_back(G64);
+        sp->go64.push_back(nullptr);
         int rc = spectrum_build(g->full, k0, g->h, G, G64, nullptr, s);
         if (rc) return bail(rc);
     }
@@ -447,32 +547,37 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
     for (const BoxSet* bs : sets) {
         const int64_t n = 6 * bs->spec_elems();
         double2* G = nullptr;
-        if (cudaMalloc(&G, n * sizeof(double2)) != cudaSuccess) {
-            cudaGetLastError();
-            return bail(fail(VIE_ENOMEM, "spectrum allocation failed"));
-        }
+        int arc = dmalloc((void**)&G, n * sizeof(double2), "vie_green_spectrum");
+        if (arc) return bail(arc);
         sp->g128.push_back(G);
         int rc = green_sample(*bs, k0, g->h, G, s);
         if (!rc) rc = spectrum_fft<double2>(*bs, G, s);
         if (rc) return bail(rc);
         float2* G64 = nullptr;
         if (mask & VIE_C64) {
-            if (cudaMalloc(&G64, n * sizeof(float2)) != cudaSuccess) {
-                cudaGetLastError();
-                return bail(fail(VIE_ENOMEM, "spectrum allocation failed"));
-            }
+            if ((arc = dmalloc((void**)&G64, n * sizeof(float2), "vie_green_spectrum"))) return bail(arc);
             if ((rc = convert_c128_to_c64(G, G64, n, s))) {
                 sp->g64.push_back(G64);
                 return bail(rc);
             }
         }
         sp->g64.push_back(G64);
+        // the slab MVM of the block solver reads an octant of the spectrum in natural order
+        float2* Go = nullptr;
+        if ((mask & VIE_C64) && slab_path_ok(*bs, sizeof(float2))) {
+            if ((arc = dmalloc((void**)&Go, 6 * bs->oct_elems() * sizeof(float2), "vie_green_spectrum")))
+                return bail(arc);
+            sp->go64.push_back(Go);
+            if ((rc = slab_spectrum(*bs, G, Go, s))) return bail(rc);
+        } else {
+            sp->go64.push_back(nullptr);
+        }
     }
     if (!(mask & VIE_C128)) {
         // the FP64 spectrum was only the source of the complex64 copy
         if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(VIE_ECUDA, "spectrum generation failed"));
         for (auto& p : sp->g128) {
-            if (p) cudaFree(p);
+            dfree(p);
             p = nullptr;
         }
     }
@@ -483,10 +588,9 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
 extern "C" int vie_spectrum_release(vie_spectrum* sp) {
     if (!sp) return fail(VIE_EINVAL, "vie_spectrum_release: null spectrum");
     cudaDeviceSynchronize();
-    for (auto p : sp->g128)
-        if (p) cudaFree(p);
-    for (auto p : sp->g64)
-        if (p) cudaFree(p);
+    for (auto p : sp->g128) dfree(p);
+    for (auto p : sp->g64) dfree(p);
+    for (auto p : sp->go64) dfree(p);
     delete sp;
     return VIE_OK;
 }
@@ -566,6 +670,7 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             j.chi = chi_of<C>(gr.bs);
             j.G = spec_of<C>(sp, 1 + i);
             j.st = gr.st;
+            if (!c128 && !slab_disabled()) j.Go = reinterpret_cast<const C*>(sp->go64[1 + i]);
             jobs.push_back(j);
         } else {
             batched.push_back(i);
@@ -860,6 +965,7 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
     VIE_TRY(vec_norm2_128(b, n3, &g->ored, g->dscal, s));
     double bn2 = 0;
     VIE_TRY(read_scalar(g, g->dscal, &bn2, s, tmo));
+    if (!std::isfinite(bn2)) return fail(VIE_EINVAL, "vie_solve: einc has non-finite entries");
     if (!(bn2 > 0.0)) x0 = nullptr;        // E_inc = 0: the solution is 0 whatever the guess
     int rc = VIE_OK;
     bool stalled = false;                  // MIXED stopped on a correction that did not help

@@ -51,11 +51,7 @@ template <class T>
 int balloc(vie_batch* b, T** p, int64_t count) {
     *p = nullptr;
     if (count <= 0) return VIE_OK;
-    cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(VIE_ENOMEM, "vie_batch: device allocation failed");
-    }
+    VIE_TRY(dmalloc((void**)p, (size_t)count * sizeof(T), "vie_batch_create"));
     b->allocations.push_back((void*)*p);
     b->device_bytes += count * (int64_t)sizeof(T);
     return VIE_OK;
@@ -63,10 +59,10 @@ int balloc(vie_batch* b, T** p, int64_t count) {
 
 void release(vie_batch* b) {
     for (auto& kv : b->spectra) {
-        cudaFree(kv.second.first);
-        cudaFree(kv.second.second);
+        dfree(kv.second.first);
+        dfree(kv.second.second);
     }
-    for (void* p : b->allocations) cudaFree(p);
+    for (void* p : b->allocations) dfree(p);
     if (b->h_scal) cudaFreeHost(b->h_scal);
     if (b->ev) cudaEventDestroy(b->ev);
     delete b;
@@ -272,10 +268,11 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
         if (it == b->spectra.end()) {
             double2* G = nullptr;
             float2* G64 = nullptr;
-            if (cudaMalloc(&G, so * sizeof(double2)) != cudaSuccess || cudaMalloc(&G64, s64 * sizeof(float2)) != cudaSuccess) {
-                cudaGetLastError();
-                if (G) cudaFree(G);
-                return fail(VIE_ENOMEM, "vie_batch_solve: spectrum allocation failed");
+            int arc = dmalloc((void**)&G, so * sizeof(double2), "vie_batch_solve");
+            if (!arc) arc = dmalloc((void**)&G64, s64 * sizeof(float2), "vie_batch_solve");
+            if (arc) {
+                dfree(G);
+                return arc;
             }
             BoxSet one = bs;
             one.nb = 1;
@@ -283,8 +280,8 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
                                     b->persistent ? G64 : nullptr, s);
             if (rc) {
                 cudaStreamSynchronize(s);
-                cudaFree(G);
-                cudaFree(G64);
+                dfree(G);
+                dfree(G64);
                 return rc;
             }
             it = b->spectra.emplace(k0s[i], std::make_pair(G, G64)).first;
@@ -303,7 +300,11 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
     VIE_CK(cudaMemcpyAsync(b->h_scal, b->d_bn2, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     VIE_CK(cudaEventRecord(b->ev, s));
     VIE_TRY(wait_ev(b->ev, tmo));
-    for (int i = 0; i < nb; ++i) bn2[i] = b->h_scal[i];
+    for (int i = 0; i < nb; ++i) {
+        bn2[i] = b->h_scal[i];
+        if (!std::isfinite(bn2[i]))
+            return fail(VIE_EINVAL, "vie_batch_solve: einc of instance " + std::to_string(i) + " has non-finite entries");
+    }
     VIE_CK(cudaMemsetAsync(x, 0, nv * sizeof(double2), s));
     VIE_TRY(vec_copy<double2>(einc, b->r128, nv, s));
     VIE_CK(cudaMemcpyAsync(b->d_rn2, b->d_bn2, nb * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -49,6 +49,12 @@ template <class C> struct InnerGroup {
     int kb_upd;                             // profiling: KB moved by the x/r update pass
     int reg;                                // 1: register-FFT MVM (complex64, every padded axis <= 32)
     unsigned fd_bx[3], fd_plane[3];         // FastDiv constants (m, s, d) for bx and bz*by
+    // slab MVM (complex64): the whole MVM on chip, kz planes of the box in shared memory
+    int slab;                               // 1: the block uses the slab MVM
+    int bxp;                                // row pitch of the slab (bx made odd: no bank conflicts)
+    int npl;                                // kz planes per round of the plane stage (set per launch)
+    unsigned fd_col[3];                     // FastDiv constants for by*bx
+    const C* Go;                            // octant spectrum [Mz/2+1][6][My/2+1][Mx/2+1], natural order
 };
 
 constexpr int kInnerThreads = 256;
@@ -632,6 +638,329 @@ struct RegMvm {
     }
 };
 
+// ---------------------------------------------------------------- slab MVM (complex64, on chip)
+// The MVM of one block without any global scratch. z is transformed first: the
+// box columns (component, y, x) go through a pruned z FFT in registers and land
+// as kz planes [3][by][bx] in the shared memory of the cluster rank that owns
+// kz (distributed shared memory stores). Each rank then takes its kz planes
+// through the x and y FFTs, the 3x3 Green multiply and the inverse x and y FFTs
+// in a shared-memory workspace, back into its slab. Last, the columns gather
+// their kz values from the owners, take the inverse z FFT in registers and
+// write v = mask (p - u) with the iteration's inner products. kz planes are
+// dealt to ranks in mirror pairs (kz, Mz - kz), so one read of the octant
+// spectrum (every component is even or odd along every axis) serves the eight
+// frequencies (+-kx, +-ky, +-kz). Two cluster barriers per MVM (R > 1), plus the
+// one inside the reduction that ends it.
+constexpr int kSlabThreads = 512;
+constexpr int kSlabBatch = 4;   // z planes per thread whose global loads are issued together
+
+// Bit reversal of k over l <= 5 bits; with constant arguments (unrolled FFT positions) it folds away.
+__host__ __device__ __forceinline__ constexpr int cbrev(int k, int l) {
+    int r = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        if (i < l) r |= ((k >> i) & 1) << (l - 1 - i);
+    return r;
+}
+
+__device__ __forceinline__ F* rank_ptr(F* p, int r, int R) {
+    return R == 1 ? p : cg::this_cluster().map_shared_rank(p, (unsigned)r);
+}
+
+// kz of slot s of rank r (P = Mz / R slots per rank): rank 0 holds the planes that are their own
+// mirrors, kz = 0 and kz = Mz/2, in slots 0 and 1, then mirror pairs (u, Mz - u) in slots
+// (2i, 2i + 1); ranks >= 1 hold mirror pairs only, in increasing u.
+__device__ __forceinline__ int slab_kz(int r, int sl, int P, int Mz) {
+    if (r == 0) {
+        if (sl < 2) return sl == 0 ? 0 : Mz / 2;
+        const int u = 1 + ((sl - 2) >> 1);
+        return (sl & 1) ? Mz - u : u;
+    }
+    const int u = (P - 2) / 2 + 1 + (r - 1) * (P / 2) + (sl >> 1);
+    return (sl & 1) ? Mz - u : u;
+}
+// Inverse of slab_kz: owner rank and slot of kz.
+__device__ __forceinline__ void slab_owner(int kz, int P, int Mz, int& r, int& sl) {
+    const int h = Mz / 2;
+    if (kz == 0 || kz == h) {
+        r = 0;
+        sl = kz == 0 ? 0 : 1;
+        return;
+    }
+    const int m = kz > h ? 1 : 0, u = m ? Mz - kz : kz, n0 = (P - 2) / 2;
+    if (u <= n0) {
+        r = 0;
+        sl = 2 + 2 * (u - 1) + m;
+        return;
+    }
+    const int q = u - n0 - 1, hp = P / 2, qr = q / hp;
+    r = 1 + qr;
+    sl = 2 * (q - qr * hp) + m;
+}
+
+// Forward half of the slab MVM: update (IN_P: p = r + c1 (p - c2 v); IN_S: s = r - c1 v), w = chi in,
+// z FFT of every box column of this rank, kz values stored into their owners' slabs.
+template <int LZ, int IN>
+__device__ __forceinline__ F slab_fwd(const InnerGroup<F>& g, int64_t voff, const F* chi, F* sm, const F* tw, F c1,
+                                      F c2) {
+    constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1, LG = ILog2<LZ>::v;
+    const int bx = g.bx, by = g.by, bz = g.bz, plane = bx * by, ncol = 3 * plane;
+    const int rk = team_rank(), R = team_size(), P = LZ / R, bxp = g.bxp, zpl = 3 * by * bxp;
+    const FastDiv dbx = fd_of(g.fd_bx), dcol = fd_of(g.fd_col);
+    const int64_t box = (int64_t)plane * bz;
+    F acc = czero<F>();
+    for (int col = rk * blockDim.x + threadIdx.x; col < ncol; col += R * blockDim.x) {
+        const int comp = (int)fdiv(col, dcol), yx = col - comp * plane;
+        const int y = (int)fdiv(yx, dbx), x = yx - y * bx;
+        const int64_t e0 = voff + comp * box + yx;
+        F a[H];
+#pragma unroll
+        for (int j0 = 0; j0 < H; j0 += kSlabBatch) {
+            F ra[kSlabBatch], pa[kSlabBatch], va[kSlabBatch], ca[kSlabBatch];
+#pragma unroll
+            for (int u = 0; u < kSlabBatch; ++u) {       // every load of the batch first
+                const int j = j0 + u;
+                if (j < H && j < bz) {
+                    const int64_t e = e0 + (int64_t)j * plane;
+                    ra[u] = g.r[e];
+                    va[u] = g.v[e];
+                    if (IN == IN_P) pa[u] = g.p[e];
+                    ca[u] = chi[j * plane + yx];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSlabBatch; ++u) {
+                const int j = j0 + u;
+                if (j >= H) continue;
+                F w = czero<F>();
+                if (j < bz) {
+                    const int64_t e = e0 + (int64_t)j * plane;
+                    F in;
+                    if (IN == IN_P) {
+                        in = ra[u] + cmul(c1, pa[u] - cmul(c2, va[u]));
+                        g.p[e] = in;
+                    } else {
+                        in = ra[u] - cmul(c1, va[u]);
+                        g.s[e] = in;
+                        acc.x += in.x * in.x + in.y * in.y;
+                    }
+                    w = cmul(in, ca[u]);
+                }
+                a[j] = w;
+            }
+        }
+        F* dst = sm + comp * by * bxp + y * bxp + x;
+        fwd_half<LZ>([&](int j) { return a[j]; },
+                     [&](int k, F v) {
+                         int r, sl;
+                         slab_owner(cbrev(k, LG), P, LZ, r, sl);
+                         *rank_ptr(dst + sl * zpl, r, R) = v;
+                     },
+                     tw);
+    }
+    return acc;
+}
+
+// 3x3 symmetric Green multiply of the point q (components cs apart) with the octant entries and the
+// sign flips of a point in the negative half of an axis (xy odd in x, y; xz in x, z; yz in y, z).
+__device__ __forceinline__ void green_pt(F* q, int cs, const F (&gv)[6], int fx, int fy, int fz) {
+    const F gxy = (fx ^ fy) ? make_float2(-gv[1].x, -gv[1].y) : gv[1];
+    const F gxz = (fx ^ fz) ? make_float2(-gv[2].x, -gv[2].y) : gv[2];
+    const F gyz = (fy ^ fz) ? make_float2(-gv[4].x, -gv[4].y) : gv[4];
+    const F X = q[0], Y = q[cs], Z = q[2 * cs];
+    q[0] = cmul(gv[0], X) + cmul(gxy, Y) + cmul(gxz, Z);
+    q[cs] = cmul(gxy, X) + cmul(gv[3], Y) + cmul(gyz, Z);
+    q[2 * cs] = cmul(gxz, X) + cmul(gyz, Y) + cmul(gv[5], Z);
+}
+
+// Plane stage: this rank's kz planes, npl at a time, through x and y FFTs, the Green multiply and
+// the inverse y and x FFTs in the workspace after the slab.
+template <int LX, int LY>
+__device__ __forceinline__ void slab_planes(const InnerGroup<F>& g, F* sm, const F* tw) {
+    constexpr int LGX = ILog2<LX>::v, LGY = ILog2<LY>::v, HX = LX / 2, HY = LY / 2;
+    const int bx = g.bx, by = g.by, Mz = g.Mz;
+    const int rk = team_rank(), R = team_size(), P = Mz / R, bxp = g.bxp, zpl = 3 * by * bxp;
+    constexpr int wp = LX + 1, cs = LY * wp, wpl = 3 * cs;
+    F* ws = sm + P * zpl;
+    const int T = blockDim.x, t = threadIdx.x;
+    constexpr int nkx = HX + 1, nky = HY + 1, ntk = nkx * nky;
+    const F* Go = g.Go;
+    for (int s0 = 0; s0 < P; s0 += g.npl) {
+        const int np = min(g.npl, P - s0);
+        const int nrow = np * 3 * by;
+        // x forward: rows (plane, component, y < by) of the slab into the workspace (natural kx)
+        for (int task = t; task < nrow; task += T) {
+            const int pc = task / by, y = task - pc * by;           // pc = plane * 3 + component
+            const F* src = sm + s0 * zpl + pc * by * bxp + y * bxp;
+            F* dst = ws + pc * cs + y * wp;
+            F in[HX];
+#pragma unroll
+            for (int j = 0; j < HX; ++j) in[j] = j < bx ? src[j] : czero<F>();
+            fwd_half<LX>([&](int j) { return in[j]; }, [&](int k, F v) { dst[cbrev(k, LGX)] = v; }, tw);
+        }
+        __syncthreads();
+        // y forward: columns (plane, component, kx), in place (natural ky)
+        const int ncw = np * 3 * LX;
+        for (int task = t; task < ncw; task += T) {
+            const int kx = task & (LX - 1), pc = task >> LGX;
+            F* colp = ws + pc * cs + kx;
+            F in[HY];
+#pragma unroll
+            for (int j = 0; j < HY; ++j) in[j] = j < by ? colp[j * wp] : czero<F>();
+            fwd_half<LY>([&](int j) { return in[j]; }, [&](int k, F v) { colp[cbrev(k, LGY) * wp] = v; }, tw);
+        }
+        __syncthreads();
+        // Green multiply: one octant entry per (pair of planes, kyf, kxf)
+        const int ntask = (np >> 1) * ntk;
+        for (int task = t; task < ntask; task += T) {
+            const int pp = task / ntk, q = task - pp * ntk;
+            const int kyf = q / nkx, kxf = q - kyf * nkx;
+            const int sa = s0 + 2 * pp;
+            const int kza = slab_kz(rk, sa, P, Mz), kzb = slab_kz(rk, sa + 1, P, Mz);
+            const int fza = kza > Mz / 2, fzb = kzb > Mz / 2;
+            const int kfa = fza ? Mz - kza : kza, kfb = fzb ? Mz - kzb : kzb;
+            F ga[6], gb[6];
+            const F* p0 = Go + ((int64_t)kfa * 6 * nky + kyf) * nkx + kxf;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) ga[c] = p0[c * ntk];
+            if (kfb != kfa) {
+                const F* p1 = Go + ((int64_t)kfb * 6 * nky + kyf) * nkx + kxf;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) gb[c] = p1[c * ntk];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) gb[c] = ga[c];
+            }
+            F* pa = ws + (2 * pp) * wpl;
+#pragma unroll
+            for (int ix = 0; ix < 2; ++ix) {
+                if (ix == 1 && (kxf == 0 || kxf == HX)) continue;
+                const int kx = ix ? LX - kxf : kxf;
+#pragma unroll
+                for (int iy = 0; iy < 2; ++iy) {
+                    if (iy == 1 && (kyf == 0 || kyf == HY)) continue;
+                    const int ky = iy ? LY - kyf : kyf;
+                    F* qa = pa + ky * wp + kx;
+                    green_pt(qa, cs, ga, ix, iy, fza);
+                    green_pt(qa + wpl, cs, gb, ix, iy, fzb);
+                }
+            }
+        }
+        __syncthreads();
+        // y inverse: columns, keep y < by
+        for (int task = t; task < ncw; task += T) {
+            const int kx = task & (LX - 1), pc = task >> LGX;
+            F* colp = ws + pc * cs + kx;
+            F st[HY];
+            inv_half<LY>([&](int k) { return colp[cbrev(k, LGY) * wp]; }, [&](int j, F v) { st[j] = v; },
+                         [&](int j) { return st[j]; },
+                         [&](int j, F v) {
+                             if (j < by) colp[j * wp] = v;
+                         },
+                         tw);
+        }
+        __syncthreads();
+        // x inverse: rows, keep x < bx, back into the slab
+        for (int task = t; task < nrow; task += T) {
+            const int pc = task / by, y = task - pc * by;
+            const F* src = ws + pc * cs + y * wp;
+            F* dst = sm + s0 * zpl + pc * by * bxp + y * bxp;
+            F st[HX];
+            inv_half<LX>([&](int k) { return src[cbrev(k, LGX)]; }, [&](int j, F v) { st[j] = v; },
+                         [&](int j) { return st[j]; },
+                         [&](int j, F v) {
+                             if (j < bx) dst[j] = v;
+                         },
+                         tw);
+        }
+        __syncthreads();
+    }
+}
+
+// Inverse half: every box column of this rank gathers its kz values from their owners, inverse z
+// FFT, out = mask (in - u) with the iteration's inner products (OUT_V: <rhat, v>; OUT_T: <t, s>, <t, t>).
+template <int LZ, int OUT>
+__device__ __forceinline__ void slab_inv(const InnerGroup<F>& g, int64_t voff, const uint8_t* mask, F* sm,
+                                         const F* tw, F& a1, F& a2) {
+    constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1, LG = ILog2<LZ>::v;
+    const int bx = g.bx, by = g.by, bz = g.bz, plane = bx * by, ncol = 3 * plane;
+    const int rk = team_rank(), R = team_size(), P = LZ / R, bxp = g.bxp, zpl = 3 * by * bxp;
+    const FastDiv dbx = fd_of(g.fd_bx), dcol = fd_of(g.fd_col);
+    const int64_t box = (int64_t)plane * bz;
+    for (int col = rk * blockDim.x + threadIdx.x; col < ncol; col += R * blockDim.x) {
+        const int comp = (int)fdiv(col, dcol), yx = col - comp * plane;
+        const int y = (int)fdiv(yx, dbx), x = yx - y * bx;
+        F* src = sm + comp * by * bxp + y * bxp + x;
+        F u[H];                                 // the stash of the FFT's upper half, then its output
+        inv_half<LZ>(
+            [&](int k) {
+                int r, sl;
+                slab_owner(cbrev(k, LG), P, LZ, r, sl);
+                return *rank_ptr(src + sl * zpl, r, R);
+            },
+            [&](int j, F v) { u[j] = v; }, [&](int j) { return u[j]; }, [&](int j, F v) { u[j] = v; }, tw);
+        const int64_t e0 = voff + comp * box + yx;
+#pragma unroll
+        for (int j0 = 0; j0 < H; j0 += kSlabBatch) {
+            F ia[kSlabBatch], ha[kSlabBatch];
+            uint8_t ma[kSlabBatch];
+#pragma unroll
+            for (int q = 0; q < kSlabBatch; ++q) {       // every load of the batch first
+                const int j = j0 + q;
+                if (j < H && j < bz) {
+                    const int64_t e = e0 + (int64_t)j * plane;
+                    ia[q] = OUT == OUT_V ? g.p[e] : g.s[e];
+                    if (OUT == OUT_V) ha[q] = g.rhat[e];
+                    ma[q] = mask[j * plane + yx];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kSlabBatch; ++q) {
+                const int j = j0 + q;
+                if (j >= H || j >= bz) continue;
+                const int64_t e = e0 + (int64_t)j * plane;
+                const F o = ma[q] ? ia[q] - u[j] : czero<F>();
+                if (OUT == OUT_V) {
+                    g.v[e] = o;
+                    acc_dot(a1, ha[q], o);
+                } else {
+                    g.t[e] = o;
+                    acc_dot(a1, o, ia[q]);
+                    a2.x += o.x * o.x + o.y * o.y;
+                }
+            }
+        }
+    }
+}
+
+struct SlabMvm {
+    template <int IN>
+    static __device__ __forceinline__ double2 fwd(const InnerGroup<F>& g, int64_t voff, F*, F*, const F* chi, F* sm,
+                                                  const F* tw, F c1, F c2, double2*) {
+        F acc = czero<F>();
+        VIE_LEN_SWITCH(g.lz, (acc = slab_fwd<LL, IN>(g, voff, chi, sm, tw, c1, c2)));
+        team_sync();                            // every rank's kz planes complete
+        return make_double2(acc.x, acc.y);      // this thread's part of ||s||^2 (IN_S), summed later
+    }
+    static __device__ __forceinline__ void mid(const InnerGroup<F>& g, F*, F* sm, const F* tw) {
+        switch (g.lx) {
+            case 3: { constexpr int AX = 8; VIE_LEN_SWITCH(g.ly, (slab_planes<AX, LL>(g, sm, tw))); } break;
+            case 4: { constexpr int AX = 16; VIE_LEN_SWITCH(g.ly, (slab_planes<AX, LL>(g, sm, tw))); } break;
+            default: { constexpr int AX = 32; VIE_LEN_SWITCH(g.ly, (slab_planes<AX, LL>(g, sm, tw))); } break;
+        }
+        team_sync();                            // every rank's planes back in its slab
+    }
+    template <int OUT>
+    static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F*, F*, const uint8_t* mask, F* sm,
+                                               const F* tw, double2* red, double2& d1, double2& d2, double extra) {
+        F a1 = czero<F>(), a2 = czero<F>();
+        VIE_LEN_SWITCH(g.lz, (slab_inv<LL, OUT>(g, voff, mask, sm, tw, a1, a2)));
+        d1 = make_double2(a1.x, a1.y);
+        d2 = make_double2(a2.x, extra);
+        team_sum2(d1, d2, red);                 // its cluster barrier also ends every read of the slabs
+    }
+};
+
 template <class C, class Mvm>
 __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, double tol, int maxit, C* sm, const C* tw,
                             double2* red, int* units) {
@@ -763,20 +1092,29 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
     __syncthreads();
 }
 
+template <bool SLAB>
 __device__ __forceinline__ void solve_dispatch(const InnerGroup<double2>& g, int b, double tol, int maxit,
                                                double2* sm, const double2* tw, double2* red, int* units) {
     solve_block<double2, SmemMvm<double2>>(g, b, tol, maxit, sm, tw, red, units);
 }
+template <bool SLAB>
 __device__ __forceinline__ void solve_dispatch(const InnerGroup<float2>& g, int b, double tol, int maxit,
                                                float2* sm, const float2* tw, double2* red, int* units) {
-    if (g.reg) solve_block<float2, RegMvm>(g, b, tol, maxit, sm, tw, red, units);
-    else solve_block<float2, SmemMvm<float2>>(g, b, tol, maxit, sm, tw, red, units);
+    if constexpr (SLAB) {
+        if (g.slab) solve_block<float2, SlabMvm>(g, b, tol, maxit, sm, tw, red, units);
+        else solve_block<float2, SmemMvm<float2>>(g, b, tol, maxit, sm, tw, red, units);
+    } else {
+        if (g.reg) solve_block<float2, RegMvm>(g, b, tol, maxit, sm, tw, red, units);
+        else solve_block<float2, SmemMvm<float2>>(g, b, tol, maxit, sm, tw, red, units);
+    }
 }
 
-template <class C>
-__global__ void __launch_bounds__(kInnerThreads, 2) k_inner(const InnerGroup<C>* groups, const int2* work, int nwork,
-                                                          int* next, double tol, int maxit, const C* tw,
-                                                          int* units) {
+// SLAB: the kernel of launches whose complex64 groups use the slab MVM (512 threads, one CTA per
+// SM); otherwise 256 threads and two CTAs per SM. npl: kz planes per round of the slab plane stage.
+template <class C, bool SLAB>
+__global__ void __launch_bounds__(SLAB ? kSlabThreads : kInnerThreads, SLAB ? 1 : 2)
+    k_inner(const InnerGroup<C>* groups, const int2* work, int nwork, int* next, double tol, int maxit, const C* tw,
+            int* units, int npl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     __shared__ double2 red[2 * (kInnerThreads / 32)];
@@ -797,9 +1135,10 @@ __global__ void __launch_bounds__(kInnerThreads, 2) k_inner(const InnerGroup<C>*
         if (threadIdx.x == 0) {
             gsh = groups[wk.x];
             if (gsh.Gb) gsh.G = gsh.Gb[wk.y];
+            gsh.npl = npl;
         }
         __syncthreads();
-        solve_dispatch(gsh, wk.y, gsh.tols ? gsh.tols[wk.y] : tol, maxit, sm, tw, red, units);
+        solve_dispatch<SLAB>(gsh, wk.y, gsh.tols ? gsh.tols[wk.y] : tol, maxit, sm, tw, red, units);
         __syncthreads();
     }
 }
@@ -820,6 +1159,14 @@ int inner_cluster_forced() {
         const char* e = getenv("VIE_INNER_CLUSTER");
         int v = e ? atoi(e) : 0;
         return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
+    }();
+    return r;
+}
+
+bool slab_disabled() {
+    static const bool r = [] {
+        const char* e = getenv("VIE_INNER_SLAB");
+        return e == nullptr || atoi(e) == 0;
     }();
     return r;
 }
@@ -863,6 +1210,23 @@ static void make_fastdiv(unsigned d, unsigned (&out)[3]) {
 }
 
 
+// Slab MVM: complex64 boxes with every padded axis in [8, 32].
+bool slab_path_ok(const BoxSet& bs, size_t es) { return reg_path_ok(bs, es); }
+constexpr size_t kSlabSmemLimit = 220 * 1024;
+// Dynamic shared memory of the slab MVM with R ranks per block and npl planes per round.
+static size_t slab_smem(const BoxSet& bs, int R, int npl) {
+    const size_t bxp = (size_t)(bs.bx | 1);
+    const size_t zb = (size_t)(bs.Mz / R) * 3 * bs.by * bxp;
+    const size_t ws = (size_t)npl * 3 * bs.My * (bs.Mx + 1);
+    return (zb + ws) * sizeof(float2);
+}
+// Smallest cluster size (1, 2 or 4) whose slab fits, or 0.
+static int slab_min_ranks(const BoxSet& bs) {
+    for (int R = 1; R <= 4; R *= 2)
+        if (bs.Mz / R >= 2 && slab_smem(bs, R, 2) <= kSlabSmemLimit) return R;
+    return 0;
+}
+
 bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force) {
     int a, b;
     size_t s;
@@ -879,6 +1243,9 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
     std::vector<InnerGroup<C>> hg(jobs.size());
     size_t smem = 0;
     int64_t bytes_per_block = 0;
+    bool any_slab = false;
+    int rmin_slab = 1;
+    std::vector<const BoxSet*> slab_sets;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const InnerJob<C>& j = jobs[i];
         const BoxSet& bs = *j.bs;
@@ -900,6 +1267,16 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         g.reg = reg_path_ok(bs, sizeof(C)) ? 1 : 0;
         make_fastdiv((unsigned)bs.bx, g.fd_bx);
         make_fastdiv((unsigned)(bs.bz * bs.by), g.fd_plane);
+        make_fastdiv((unsigned)(bs.by * bs.bx), g.fd_col);
+        g.slab = (j.Go != nullptr && slab_path_ok(bs, sizeof(C)) && slab_min_ranks(bs) > 0) ? 1 : 0;
+        g.bxp = bs.bx | 1;
+        g.npl = 2;
+        g.Go = j.Go;
+        if (g.slab) {
+            any_slab = true;
+            rmin_slab = std::max(rmin_slab, slab_min_ranks(bs));
+            slab_sets.push_back(&bs);
+        }
         if (g.reg) sm = reg_smem(bs);
         // algorithmic bytes of one MVM with its fused vector work: plane spectra written, read and
         // rewritten along z, read back (4 x [3][bz][My][Mx]), the Green spectrum once, chi and mask,
@@ -907,8 +1284,9 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         const int64_t es = sizeof(C), box = bs.box_elems();
         const int64_t w2b = 3LL * bs.bz * bs.My * bs.Mx * es;
         const int64_t w1b = 3LL * bs.bz * bs.by * bs.Mx * es;
-        const int64_t mvm = g.reg ? 4 * w1b + 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 7 * 3 * box * es
-                                  : 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 4 * 3 * box * es;
+        const int64_t mvm = g.slab ? 6LL * bs.oct_elems() * es + box * (es + 1) + 7 * 3 * box * es
+                            : g.reg ? 4 * w1b + 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 7 * 3 * box * es
+                                    : 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 4 * 3 * box * es;
         g.kb_mvm = (int)((mvm + 1023) / 1024);
         g.kb_upd = (int)((6 * 3 * box * es + 1023) / 1024);
         smem = std::max(smem, sm);
@@ -918,10 +1296,23 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
     VIE_CK(cudaMemcpyAsync(d_groups, hg.data(), hg.size() * sizeof(InnerGroup<C>), cudaMemcpyHostToDevice, s));
     const bool two = split != nullptr && split->nheavy > 0 && split->nheavy < nwork && !inner_cluster_forced();
     VIE_CK(cudaMemsetAsync(d_next, 0, (two ? 2 : 1) * sizeof(int), s));
-    // opt in to the exact dynamic size: the default 48 KB limit also counts the static shared memory
-    VIE_CK(cudaFuncSetAttribute(k_inner<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = any_slab ? k_inner<C, true> : k_inner<C, false>;
+    // dynamic shared memory and planes per round of a launch with R CTAs per block
+    auto launch_smem = [&](int R, int* npl) -> size_t {
+        size_t m = smem;
+        *npl = 4;
+        for (const BoxSet* b : slab_sets)
+            if (slab_smem(*b, R, 4) > kSlabSmemLimit) *npl = 2;
+        for (const BoxSet* b : slab_sets) m = std::max(m, slab_smem(*b, R, *npl));
+        return m;
+    };
     // one block per cluster of R CTAs; as many clusters as fit at once, pulling blocks from the queue
     auto launch = [&](const int2* work, int n, int* next, int R, cudaStream_t st, int* units) -> int {
+        if (any_slab) R = std::max(R, rmin_slab);
+        int npl = 2;
+        const size_t sm_bytes = launch_smem(R, &npl);
+        // opt in to the exact dynamic size: the default 48 KB limit also counts the static shared memory
+        VIE_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes));
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = R;
@@ -929,16 +1320,17 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         attr[0].val.clusterDim.z = 1;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(R);
-        cfg.blockDim = dim3(kInnerThreads);
-        cfg.dynamicSmemBytes = smem;
+        cfg.blockDim = dim3(any_slab ? kSlabThreads : kInnerThreads);
+        cfg.dynamicSmemBytes = sm_bytes;
         cfg.stream = st;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        VIE_CK(cudaOccupancyMaxActiveClusters(&nclusters, k_inner<C>, &cfg));
+        VIE_CK(cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg));
+        if (nclusters < 1) return fail(VIE_EINVAL, "block solver: no cluster of this size fits on the device");
         cfg.gridDim = dim3(std::max(1, std::min(n, nclusters)) * R);
-        cudaError_t le = cudaLaunchKernelEx(&cfg, k_inner<C>, reinterpret_cast<const InnerGroup<C>*>(d_groups), work,
-                                            n, next, tol, maxit, tw_of<C>(tw), units);
+        cudaError_t le = cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<const InnerGroup<C>*>(d_groups), work, n,
+                                            next, tol, maxit, tw_of<C>(tw), units, npl);
         if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchKernelEx(k_inner)", __FILE__, __LINE__);
         return VIE_OK;
     };
@@ -971,6 +1363,30 @@ template int inner_persistent<double2>(const std::vector<InnerJob<double2>>&, co
                                        int, cudaStream_t, int, const InnerSplit*);
 template int inner_persistent<float2>(const std::vector<InnerJob<float2>>&, const int2*, int, void*, int*, double, int,
                                       cudaStream_t, int, const InnerSplit*);
+
+__global__ void k_slab_spectrum(const double2* __restrict__ G, float2* __restrict__ Go, int Mx, int My, int Mz, int lx,
+                                int ly, int lz) {
+    const int nkx = Mx / 2 + 1, nky = My / 2 + 1, nkz = Mz / 2 + 1;
+    const int64_t n = (int64_t)nkz * 6 * nky * nkx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % nkx);
+        int64_t t = i / nkx;
+        const int ky = (int)(t % nky);
+        t /= nky;
+        const int c = (int)(t % 6), kz = (int)(t / 6);
+        const int64_t px = bit_reverse(kx, lx), py = bit_reverse(ky, ly), pz = bit_reverse(kz, lz);
+        const double2 v = G[((c * (int64_t)Mz + pz) * My + py) * Mx + px];
+        Go[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+int slab_spectrum(const BoxSet& bs, const double2* G, float2* Go, cudaStream_t s) {
+    const int64_t n = 6 * bs.oct_elems();
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_slab_spectrum<<<blocks, 256, 0, s>>>(G, Go, bs.Mx, bs.My, bs.Mz, bs.lx, bs.ly, bs.lz);
+    VIE_CK(cudaGetLastError());
+    return VIE_OK;
+}
 
 size_t inner_group_desc_bytes() { return std::max(sizeof(InnerGroup<double2>), sizeof(InnerGroup<float2>)); }
 

@@ -55,6 +55,9 @@ int scratch_address(unsigned char** out) {
         tw[m] = make_double2((double)cosl(th), (double)-sinl(th));
     }
     VIE_CK(cudaMemcpy(p, tw, kTwBytes, cudaMemcpyHostToDevice));
+    // a copy from pageable memory may return before its DMA lands, and the caller's stream may be
+    // a non-blocking one that does not wait for the legacy stream: wait for the table here
+    VIE_CK(cudaDeviceSynchronize());
     g_addr[dev] = static_cast<unsigned char*>(p);
     *out = static_cast<unsigned char*>(p);
     return VIE_OK;
@@ -104,6 +107,9 @@ extern "C" int vie_matvec_noalloc(int32_t nx, int32_t ny, int32_t nz, double h, 
     const char* xa = reinterpret_cast<const char*>(x_dev);
     const char* ya = reinterpret_cast<const char*>(y_dev);
     if (xa < ya + n3 * 16 && ya < xa + n3 * 16) return fail(VIE_EINVAL, "vie_matvec_noalloc: x and y overlap");
+    const char* ca = reinterpret_cast<const char*>(chi_dev);
+    const int64_t nchi = (int64_t)nx * ny * nz * 16;
+    if (ca < ya + n3 * 16 && ya < ca + nchi) return fail(VIE_EINVAL, "vie_matvec_noalloc: chi and y overlap");
 
     unsigned char* base = nullptr;
     VIE_TRY(scratch_address(&base));

@@ -69,6 +69,13 @@ struct Twiddles {              // W_Lmax^m = exp(-2 pi i m / Lmax), m in [0, Lma
 };
 int get_twiddles(Twiddles* out);   // per device, created on first use
 
+// Counted device allocations of the library's handles (grids, spectra, batches).
+// dmalloc refuses with VIE_EBUSY, allocating nothing, when the bytes held would
+// exceed the budget set by vie_set_device_budget (0 = none); a failing
+// cudaMalloc gives VIE_ENOMEM. dfree returns the bytes of a pointer dmalloc gave.
+int dmalloc(void** p, size_t bytes, const char* what);
+void dfree(void* p);
+
 // A batch of equal-shaped boxes sharing one padded FFT shape. The full-grid
 // operator is the batch with nb = 1 and the box equal to the grid.
 struct BoxSet {
@@ -183,6 +190,8 @@ struct vie_spectrum {
     // frequency positions per axis), scaled by 1/(Mx My Mz).
     std::vector<double2*> g128;
     std::vector<float2*> g64;
+    // index 1 + g: complex64 octant spectrum of group g in natural order for the slab MVM, or null
+    std::vector<float2*> go64;
 };
 
 struct vie_grid {
@@ -306,8 +315,13 @@ template <class C> struct InnerJob {
     SegState* st;
     const C* const* Gb = nullptr;   // optional device array: one spectrum per box
     const double* tols = nullptr;   // optional device array: one relative tolerance per box
+    const C* Go = nullptr;          // optional octant spectrum in natural order (slab MVM, complex64)
 };
 bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force);
+bool slab_path_ok(const BoxSet& bs, size_t es);
+// Octant spectrum of the slab MVM from a full FP64 spectrum [6][Mz][My][Mx] (bit-reversed positions):
+// Go[kz][c][ky][kx] = G[c][brev(kz)][brev(ky)][brev(kx)] for k in [0, M/2] per axis, as complex64.
+int slab_spectrum(const BoxSet& bs, const double2* G, float2* Go, cudaStream_t s);
 size_t inner_group_desc_bytes();
 // cluster: CTAs per block (1, 2, 4, 8; 0 = 2), unless VIE_INNER_CLUSTER forces one.
 // Split launch (split != null, 0 < split->nheavy < nwork): the first nheavy work items run
@@ -324,6 +338,8 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
                      int* d_next, double tol, int maxit, cudaStream_t s, int cluster = 0,
                      const InnerSplit* split = nullptr);
 int inner_cluster_forced();
+// True when the environment variable VIE_INNER_SLAB is 0: complex64 blocks keep the register-FFT MVM.
+bool slab_disabled();
 template <class C> inline const C* tw_of(const Twiddles& t);
 template <> inline const double2* tw_of<double2>(const Twiddles& t) { return t.d128; }
 template <> inline const float2* tw_of<float2>(const Twiddles& t) { return t.d64; }

@@ -112,6 +112,9 @@ def load(path=LIB_PATH):
         "vie_batch_get_info": ([P, POINTER(c_int64), POINTER(c_int32)], c_int),
         "vie_profile_enable": ([c_int], c_int),
         "vie_profile_read": ([POINTER(KernelStat), c_int, POINTER(c_int), POINTER(c_int64)], c_int),
+        "vie_set_device_budget": ([c_int64], c_int),
+        "vie_device_usage": ([POINTER(c_int64), POINTER(c_int64)], c_int),
+        "vie_fault_inject_alloc": ([c_int32], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -159,6 +162,18 @@ def launch_count():
     tot = c_int64()
     _check(load().vie_profile_read(None, 0, None, byref(tot)))
     return tot.value
+
+
+def set_device_budget(nbytes):
+    """Process-wide cap on the device bytes held by grids, spectra and batches (0: none)."""
+    _check(load().vie_set_device_budget(int(nbytes)))
+
+
+def device_usage():
+    """(bytes held by the library's handles, budget) on the device."""
+    held, budget = c_int64(), c_int64()
+    _check(load().vie_device_usage(byref(held), byref(budget)))
+    return held.value, budget.value
 
 
 def _stream():

@@ -6,7 +6,10 @@ block on the driver's allocator). vie_matvec_noalloc keeps every intermediate
 in one static device array instead. This test calls it through the C ABI and
 checks it against vie_matvec (the allocating path) to the complex128 MVM
 tolerance, on two calls in a row so that state left in the shared array by one
-call cannot leak into the next. It lives in its own file, collected last.
+call cannot leak into the next, and on its own against the CPU oracle's FFT
+operator. It lives in its own file, collected last; its first test makes the
+first call of the process on a non-blocking side stream (the one-time twiddle
+upload must be complete before that stream's kernels read it).
 """
 import ctypes
 
@@ -14,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import mvm as omvm
 from paper_2501_13512_gb300 import inputs, vie
 
 pytestmark = pytest.mark.gpu
@@ -30,6 +34,22 @@ def _noalloc(lib, n, chi, x, y):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     return lib.vie_matvec_noalloc(n[0], n[1], n[2], H, K0, ctypes.c_void_p(chi.data_ptr()),
                                   ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), stream)
+
+
+@pytest.mark.parametrize("n,seed", [((5, 7, 3), 6), ((1, 9, 4), 7)])
+def test_noalloc_matches_oracle_on_a_side_stream(n, seed):
+    # the first no-allocation call of a fresh process runs here, on a non-blocking side stream
+    lib = vie.load()
+    eps_r, _, x = inputs.random_case(n, seed=seed)
+    ref = omvm.FFTOperator(eps_r, H, K0)(x)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        xd, chi = _dev(x), _dev(eps_r - 1.0)
+        y = torch.full_like(xd, complex(np.nan, np.nan))
+        assert _noalloc(lib, n, chi, xd, y) == vie.VIE_OK, vie.last_error()
+    side.synchronize()
+    got = y.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
 @pytest.mark.parametrize("n,seed", [((16, 16, 16), 1), ((5, 7, 3), 2), ((1, 9, 4), 3)])
@@ -69,3 +89,9 @@ def test_noalloc_after_a_different_grid_and_rejects_oversize():
     chi = torch.zeros((16, 16, 17), dtype=torch.complex128, device="cuda")
     assert _noalloc(lib, big, chi, z, torch.empty_like(z)) == vie.VIE_EINVAL
     assert "static scratch limit" in vie.last_error()
+    # y overlapping chi is refused before any launch
+    n = (4, 4, 4)
+    buf = torch.zeros(3 * 64 + 64, dtype=torch.complex128, device="cuda")
+    x = torch.zeros(3 * 64, dtype=torch.complex128, device="cuda")
+    assert _noalloc(lib, n, buf[3 * 64 - 8:], x, buf[:3 * 64]) == vie.VIE_EINVAL
+    assert "chi and y overlap" in vie.last_error()
