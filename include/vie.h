@@ -99,9 +99,10 @@ typedef struct {
     int32_t Mx, My, Mz;      /* padded FFT shape of the full-grid operator         */
     int64_t device_bytes;    /* device memory held by the grid handle              */
     int32_t inner_cluster[2];/* CTAs per block chosen by the block solver's tuner for
-                                complex128 [0] and complex64 [1]: 2 or 4 for every
-                                block, -1 for the split launch (4 for the slowest
-                                blocks, 2 for the rest); 0 = not yet tuned          */
+                                complex128 [0] and complex64 [1]: 1, 2 or 4 for
+                                every block, -1 for the split launch (the slowest
+                                blocks on 4 CTAs and the rest on 2, or on 2 and 1
+                                for the on-chip complex64 MVM); 0 = not yet tuned  */
 } vie_grid_info;
 
 /* Creates the grid on the current CUDA device: uploads chi = eps_r - 1,

@@ -19,7 +19,7 @@ HEADERS = [os.path.join(CSRC, "vie_internal.cuh"), os.path.join(CSRC, "fft_core.
 LIB = os.path.join(HERE, "libvie.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
-                "-I" + os.path.join(ROOT, "include")]
+                "-I" + os.path.join(ROOT, "include")] + os.environ.get("VIE_NVCC_FLAGS", "").split()
 
 
 def nvcc_path():

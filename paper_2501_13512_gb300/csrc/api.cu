@@ -676,22 +676,29 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             batched.push_back(i);
         }
     }
-    // cluster size: candidates 2 and 4 for every block, then the split launch (4 for the slowest
-    // blocks of the previous apply, 2 for the rest), tried on the first three applies; then the best
+    // cluster size: two candidates for every block, then the split launch (the slowest blocks of the
+    // previous apply on the larger cluster, the rest on the smaller one), tried on the first three
+    // applies; then the best. Register-FFT MVM: 2, 4, split 4/2. Slab MVM (whole MVM on chip, the
+    // cluster splits the kz planes): 2, 1, 4 (a split cannot shorten the slowest block's solve, which
+    // bounds the apply once every block fits on the device at once).
+    bool slab = false;
+    for (const InnerJob<C>& j : jobs) slab = slab || j.Go != nullptr;
     static const int kCand[3] = {2, 4, -1};
+    static const int kCandSlab[3] = {2, 1, 4};
     const int pi = c128 ? 0 : 1;
     const int tried = g->tune_count[pi];
     const bool tuning = !jobs.empty() && tried < 3 && !inner_cluster_forced();
-    const int choice = tuning ? kCand[tried] : (g->tune_best[pi] ? g->tune_best[pi] : 2);
+    const int choice = tuning ? (slab ? kCandSlab : kCand)[tried] : (g->tune_best[pi] ? g->tune_best[pi] : 2);
     InnerSplit split;
     split.nheavy = choice == -1 ? g->nheavy[pi] : 0;
-    split.cluster = 4;
+    split.cluster = slab ? 2 : 4;
     split.s2 = g->s2;
     split.fork = g->fork_ev;
     split.join = g->join_ev;
     if (tuning) VIE_CK(cudaEventRecord(g->tev[0], s));
     VIE_TRY(inner_persistent<C>(jobs, c128 ? g->work128 : g->work64, c128 ? g->nwork128 : g->nwork64,
-                                g->inner_groups, g->inner_next, tol, maxit, s, choice == -1 ? 2 : choice, &split));
+                                g->inner_groups, g->inner_next, tol, maxit, s,
+                                choice == -1 ? (slab ? 1 : 2) : choice, &split));
     if (tuning) VIE_CK(cudaEventRecord(g->tev[1], s));
     std::vector<Bicg<C>> bk(ng);
     for (int i : batched) {
@@ -799,7 +806,7 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             int best = 0;
             for (int k = 1; k < 3; ++k)
                 if (g->tune_score[pi][k] < g->tune_score[pi][best]) best = k;
-            g->tune_best[pi] = kCand[best];
+            g->tune_best[pi] = (slab ? kCandSlab : kCand)[best];
         }
     }
     return VIE_OK;

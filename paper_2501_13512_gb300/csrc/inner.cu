@@ -59,9 +59,6 @@ template <class C> struct InnerGroup {
 
 constexpr int kInnerThreads = 256;
 
-template <class C> __device__ __forceinline__ double2 wide(C a);
-template <> __device__ __forceinline__ double2 wide<double2>(double2 a) { return a; }
-template <> __device__ __forceinline__ double2 wide<float2>(float2 a) { return make_double2(a.x, a.y); }
 
 __device__ __forceinline__ double2 dcdiv(double2 a, double2 b) {
     double d = b.x * b.x + b.y * b.y;
@@ -73,27 +70,6 @@ __device__ __forceinline__ bool dgood(double2 a) {
 template <class C> __device__ __forceinline__ void acc_dot(C& acc, C a, C b) {   // acc += conj(a) b
     acc.x += a.x * b.x + a.y * b.y;
     acc.y += a.x * b.y - a.y * b.x;
-}
-
-// CTA-wide sum of two complex values (FP64), returned to every thread.
-__device__ void cta_sum2(double2& a, double2& b, double2* red) {
-    for (int o = 16; o > 0; o >>= 1) {
-        a.x += __shfl_down_sync(0xffffffffu, a.x, o);
-        a.y += __shfl_down_sync(0xffffffffu, a.y, o);
-        b.x += __shfl_down_sync(0xffffffffu, b.x, o);
-        b.y += __shfl_down_sync(0xffffffffu, b.y, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (l == 0) { red[2 * w] = a; red[2 * w + 1] = b; }
-    __syncthreads();
-    double2 sa = make_double2(0, 0), sb = make_double2(0, 0);
-    for (int i = 0; i < nw; ++i) {   // fixed order: identical result in every thread
-        sa.x += red[2 * i].x; sa.y += red[2 * i].y;
-        sb.x += red[2 * i + 1].x; sb.y += red[2 * i + 1].y;
-    }
-    a = sa;
-    b = sb;
 }
 
 // A block is solved by a team: the R CTAs of one thread-block cluster. Every
@@ -109,31 +85,61 @@ __device__ __forceinline__ void team_sync() { cg::this_cluster().sync(); }
 // ranks of a cluster flip in step.
 __shared__ int team_slot;
 
-// Two slots alternate between consecutive sums: a slot is rewritten two sums
-// later, after every rank has passed the barrier of the sum in between (by
-// which time all reads of the slot are done), so one barrier per sum suffices.
-__device__ void team_sum2(double2& a, double2& b, double2* red) {
-    cta_sum2(a, b, red);
+template <class T> __device__ __forceinline__ T shfl_dn(T v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+
+// Team-wide sums of two complex partials a and b held by every thread (complex64
+// or complex128). Each warp adds its lanes in the partials' precision; thread 0
+// adds the warps' sums in FP64 in a fixed order (and, for R > 1, the ranks' sums
+// in rank order through distributed shared memory), then calls fn(sum_a, sum_b):
+// the iteration's FP64 scalar work runs in that one thread and reaches the others
+// through the shared state fn writes, published by the closing barrier. Every rank
+// computes identical sums. Two rank slots alternate between consecutive sums: a
+// slot is rewritten two sums later, after every rank has passed the cluster
+// barrier of the sum in between, so one cluster barrier per sum suffices.
+template <class C, class Fn>
+__device__ __forceinline__ void team_sum(C a, C b, double2* red, Fn fn) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a.x += shfl_dn(a.x, o);
+        a.y += shfl_dn(a.y, o);
+        b.x += shfl_dn(b.x, o);
+        b.y += shfl_dn(b.y, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) {
+        red[2 * w] = make_double2(a.x, a.y);
+        red[2 * w + 1] = make_double2(b.x, b.y);
+    }
+    __syncthreads();
     cg::cluster_group cl = cg::this_cluster();
     const unsigned R = cl.num_blocks();
-    if (R == 1) return;
     __shared__ double2 xred[2][2];
-    if (threadIdx.x == 0) team_slot ^= 1;  // every rank flips in step (same call sequence)
-    __syncthreads();
-    const int sl = team_slot;
-    if (threadIdx.x == 0) {
-        xred[sl][0] = a;
-        xred[sl][1] = b;
-    }
-    cl.sync();
     double2 sa = make_double2(0, 0), sb = make_double2(0, 0);
-    for (unsigned r = 0; r < R; ++r) {
-        const double2* q = cl.map_shared_rank(&xred[sl][0], r);
-        sa.x += q[0].x; sa.y += q[0].y;
-        sb.x += q[1].x; sb.y += q[1].y;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < nw; ++i) {
+            sa.x += red[2 * i].x; sa.y += red[2 * i].y;
+            sb.x += red[2 * i + 1].x; sb.y += red[2 * i + 1].y;
+        }
+        if (R > 1) {
+            team_slot ^= 1;
+            xred[team_slot][0] = sa;
+            xred[team_slot][1] = sb;
+        }
     }
-    a = sa;
-    b = sb;
+    if (R > 1) {
+        cl.sync();
+        if (threadIdx.x == 0) {
+            sa = make_double2(0, 0);
+            sb = make_double2(0, 0);
+            for (unsigned r = 0; r < R; ++r) {
+                const double2* q = cl.map_shared_rank(&xred[team_slot][0], r);
+                sa.x += q[0].x; sa.y += q[0].y;
+                sb.x += q[1].x; sb.y += q[1].y;
+            }
+        }
+    }
+    if (threadIdx.x == 0) fn(sa, sb);
+    __syncthreads();
 }
 
 enum { IN_P = 0, IN_S = 1 };
@@ -142,8 +148,7 @@ enum { OUT_V = 0, OUT_T = 1 };
 // Phase XY: plane tiles, fused vector update + chi, 2D forward FFT, store spectrum.
 // IN_P: p = r + beta (p - omega v);  IN_S: s = r - alpha v (returns ||s||^2 in .x).
 template <class C, int IN>
-__device__ double2 phase_xy(const InnerGroup<C>& g, int64_t voff, C* W, const C* chi, C* sm, const C* tw,
-                            C c1, C c2, double2* red) {
+__device__ C phase_xy(const InnerGroup<C>& g, int64_t voff, C* W, const C* chi, C* sm, const C* tw, C c1, C c2) {
     const int planes = 3 * g.bz, P = g.Mx + 1, pe = g.My * P, tile = 1 << g.lpt;
     const int64_t box = (int64_t)g.bx * g.by * g.bz;
     C acc = czero<C>();
@@ -183,7 +188,7 @@ __device__ double2 phase_xy(const InnerGroup<C>& g, int64_t voff, C* W, const C*
         }
         __syncthreads();
     }
-    return wide<C>(acc);   // this thread's partial; the caller folds it into a later sum
+    return acc;   // this thread's partial; the caller folds it into a later sum
 }
 
 // Phase Z: forward FFT along z, Green multiply, inverse FFT (columns of the plane spectra).
@@ -231,10 +236,9 @@ __device__ void phase_z(const InnerGroup<C>& g, C* W, C* sm, const C* tw) {
 // OUT_V: in = p, out = v, returns <rhat, v>.  OUT_T: in = s, out = t, returns (<t, s>, <t, t>).
 template <class C, int OUT>
 __device__ void phase_xy_inv(const InnerGroup<C>& g, int64_t voff, const C* W, const uint8_t* mask, C* sm,
-                             const C* tw, double2* red, double2& d1, double2& d2, double extra) {
+                             const C* tw, C& a1, C& a2) {
     const int planes = 3 * g.bz, P = g.Mx + 1, pe = g.My * P, tile = 1 << g.lpt;
     const int64_t box = (int64_t)g.bx * g.by * g.bz;
-    C a1 = czero<C>(), a2 = czero<C>();
     const int rk = team_rank(), nrk = team_size();
     for (int pl0 = rk * tile; pl0 < planes; pl0 += nrk * tile) {
         const int n = tile * g.My * g.Mx;
@@ -270,10 +274,6 @@ __device__ void phase_xy_inv(const InnerGroup<C>& g, int64_t voff, const C* W, c
         }
         __syncthreads();
     }
-    d1 = wide<C>(a1);
-    d2 = wide<C>(a2);
-    d2.y = extra;          // deferred sum (||s||^2) rides in the unused imaginary slot
-    team_sum2(d1, d2, red);
 }
 
 // ---------------------------------------------------------------- register-FFT box MVM (complex64)
@@ -291,6 +291,11 @@ __device__ __forceinline__ void cp_async8(F* dst_smem, const F* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// 16-byte asynchronous copy global -> shared, bypassing L1 (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
 
 // Prefetch into L1: lets a loop with one pending element per thread overlap
 // the L2 latency of later iterations without holding their values in registers.
@@ -592,10 +597,11 @@ __device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, 
 
 // The two MVM implementations used by solve_block.
 template <class C> struct SmemMvm {
+    static constexpr int kUV = 1;       // elements per thread per batch in the block-vector passes
     template <int IN>
-    static __device__ double2 fwd(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const C* chi, C* sm,
-                                  const C* tw, C c1, C c2, double2* red) {
-        double2 r = phase_xy<C, IN>(g, voff, W2, chi, sm, tw, c1, c2, red);
+    static __device__ C fwd(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const C* chi, C* sm, const C* tw,
+                            C c1, C c2) {
+        C r = phase_xy<C, IN>(g, voff, W2, chi, sm, tw, c1, c2);
         team_sync();
         return r;                                 // this thread's part of ||s||^2 (IN_S)
     }
@@ -603,38 +609,36 @@ template <class C> struct SmemMvm {
         phase_z<C>(g, W2, sm, tw);
         team_sync();
     }
+    // this thread's partials of the iteration's inner products
     template <int OUT>
     static __device__ void inv(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const uint8_t* mask, C* sm,
-                               const C* tw, double2* red, double2& d1, double2& d2, double extra) {
-        phase_xy_inv<C, OUT>(g, voff, W2, mask, sm, tw, red, d1, d2, extra);
+                               const C* tw, C& a1, C& a2) {
+        phase_xy_inv<C, OUT>(g, voff, W2, mask, sm, tw, a1, a2);
     }
 };
 
 struct RegMvm {
+    static constexpr int kUV = 1;
     template <int IN>
-    static __device__ __forceinline__ double2 fwd(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const F* chi, F* sm,
-                                  const F* tw, F c1, F c2, double2* red) {
+    static __device__ __forceinline__ F fwd(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const F* chi, F* sm,
+                                            const F* tw, F c1, F c2) {
         F acc = czero<F>();
         VIE_LEN_SWITCH(g.lx, (acc = x_fwd_reg<LL, IN>(g, voff, W1, chi, sm, tw, c1, c2)));
         team_sync();
         VIE_LEN_SWITCH(g.ly, (y_fwd_reg<LL>(g, W1, W2, tw)));
         team_sync();                            // W2 complete on every rank
-        return make_double2(acc.x, acc.y);      // this thread's part of ||s||^2 (IN_S), summed later
+        return acc;                             // this thread's part of ||s||^2 (IN_S), summed later
     }
     static __device__ __forceinline__ void mid(const InnerGroup<F>& g, F* W2, F* sm, const F* tw) {
         VIE_LEN_SWITCH(g.lz, (z_reg<LL>(g, W2, sm, tw)));
         team_sync();
     }
     template <int OUT>
-    static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const uint8_t* mask, F* sm,
-                               const F* tw, double2* red, double2& d1, double2& d2, double extra) {
+    static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const uint8_t* mask,
+                                               F* sm, const F* tw, F& a1, F& a2) {
         VIE_LEN_SWITCH(g.ly, (y_inv_reg<LL>(g, W2, W1, tw)));
         team_sync();
-        F a1 = czero<F>(), a2 = czero<F>();
         VIE_LEN_SWITCH(g.lx, (x_inv_reg<LL, OUT>(g, voff, W1, mask, sm, tw, a1, a2)));
-        d1 = make_double2(a1.x, a1.y);
-        d2 = make_double2(a2.x, extra);          // .y carries a deferred sum (||s||^2)
-        team_sum2(d1, d2, red);
     }
 };
 
@@ -651,8 +655,19 @@ struct RegMvm {
 // spectrum (every component is even or odd along every axis) serves the eight
 // frequencies (+-kx, +-ky, +-kz). Two cluster barriers per MVM (R > 1), plus the
 // one inside the reduction that ends it.
-constexpr int kSlabThreads = 512;
-constexpr int kSlabBatch = 4;   // z planes per thread whose global loads are issued together
+#ifndef VIE_SLAB_THREADS
+#define VIE_SLAB_THREADS 256
+#endif
+constexpr int kSlabThreads = VIE_SLAB_THREADS;
+// The three stages of the slab MVM are separate functions (each allocates its own registers) unless
+// VIE_SLAB_INLINE is defined as __forceinline__.
+#ifndef VIE_SLAB_INLINE
+#define VIE_SLAB_INLINE __noinline__
+#endif
+#ifndef VIE_SLAB_BATCH
+#define VIE_SLAB_BATCH 4
+#endif
+constexpr int kSlabBatch = VIE_SLAB_BATCH;   // z planes per thread whose global loads are issued together
 
 // Bit reversal of k over l <= 5 bits; with constant arguments (unrolled FFT positions) it folds away.
 __host__ __device__ __forceinline__ constexpr int cbrev(int k, int l) {
@@ -698,14 +713,28 @@ __device__ __forceinline__ void slab_owner(int kz, int P, int Mz, int& r, int& s
     sl = 2 * (q - qr * hp) + m;
 }
 
+// Per kz: generic address of its plane in the slab of the rank that owns it (local or distributed
+// shared memory), so the unrolled column transforms index a table instead of mapping ranks.
+__shared__ F* slab_tab[32];
+
+__device__ __forceinline__ void slab_table(const InnerGroup<F>& g, F* sm) {
+    const int R = team_size(), Mz = g.Mz, P = Mz / R, zpl = 3 * g.by * g.bxp;
+    if ((int)threadIdx.x < Mz) {
+        int r, sl;
+        slab_owner(threadIdx.x, P, Mz, r, sl);
+        slab_tab[threadIdx.x] = rank_ptr(sm + sl * zpl, r, R);
+    }
+    __syncthreads();
+}
+
 // Forward half of the slab MVM: update (IN_P: p = r + c1 (p - c2 v); IN_S: s = r - c1 v), w = chi in,
 // z FFT of every box column of this rank, kz values stored into their owners' slabs.
 template <int LZ, int IN>
-__device__ __forceinline__ F slab_fwd(const InnerGroup<F>& g, int64_t voff, const F* chi, F* sm, const F* tw, F c1,
+__device__ VIE_SLAB_INLINE F slab_fwd(const InnerGroup<F>& g, int64_t voff, const F* chi, F* sm, const F* tw, F c1,
                                       F c2) {
     constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1, LG = ILog2<LZ>::v;
     const int bx = g.bx, by = g.by, bz = g.bz, plane = bx * by, ncol = 3 * plane;
-    const int rk = team_rank(), R = team_size(), P = LZ / R, bxp = g.bxp, zpl = 3 * by * bxp;
+    const int rk = team_rank(), R = team_size(), bxp = g.bxp;
     const FastDiv dbx = fd_of(g.fd_bx), dcol = fd_of(g.fd_col);
     const int64_t box = (int64_t)plane * bz;
     F acc = czero<F>();
@@ -749,17 +778,14 @@ __device__ __forceinline__ F slab_fwd(const InnerGroup<F>& g, int64_t voff, cons
                 a[j] = w;
             }
         }
-        F* dst = sm + comp * by * bxp + y * bxp + x;
-        fwd_half<LZ>([&](int j) { return a[j]; },
-                     [&](int k, F v) {
-                         int r, sl;
-                         slab_owner(cbrev(k, LG), P, LZ, r, sl);
-                         *rank_ptr(dst + sl * zpl, r, R) = v;
-                     },
-                     tw);
+        const int off = comp * by * bxp + y * bxp + x;
+        fwd_half<LZ>([&](int j) { return a[j]; }, [&](int k, F v) { slab_tab[cbrev(k, LG)][off] = v; }, tw);
     }
     return acc;
 }
+
+// Offset (in complex64 entries) of the staged spectrum rows after `used` entries: 16-byte aligned.
+__host__ __device__ __forceinline__ int slab_gs_offset(int used) { return (used + 1) & ~1; }
 
 // 3x3 symmetric Green multiply of the point q (components cs apart) with the octant entries and the
 // sign flips of a point in the negative half of an axis (xy odd in x, y; xz in x, z; yz in y, z).
@@ -776,7 +802,7 @@ __device__ __forceinline__ void green_pt(F* q, int cs, const F (&gv)[6], int fx,
 // Plane stage: this rank's kz planes, npl at a time, through x and y FFTs, the Green multiply and
 // the inverse y and x FFTs in the workspace after the slab.
 template <int LX, int LY>
-__device__ __forceinline__ void slab_planes(const InnerGroup<F>& g, F* sm, const F* tw) {
+__device__ VIE_SLAB_INLINE void slab_planes(const InnerGroup<F>& g, F* sm, const F* tw) {
     constexpr int LGX = ILog2<LX>::v, LGY = ILog2<LY>::v, HX = LX / 2, HY = LY / 2;
     const int bx = g.bx, by = g.by, Mz = g.Mz;
     const int rk = team_rank(), R = team_size(), P = Mz / R, bxp = g.bxp, zpl = 3 * by * bxp;
@@ -785,9 +811,27 @@ __device__ __forceinline__ void slab_planes(const InnerGroup<F>& g, F* sm, const
     const int T = blockDim.x, t = threadIdx.x;
     constexpr int nkx = HX + 1, nky = HY + 1, ntk = nkx * nky;
     const F* Go = g.Go;
+    // octant spectrum rows of the round's kz pairs, staged in shared memory while x and y transform
+    F* gs = sm + slab_gs_offset(P * zpl + g.npl * wpl);
     for (int s0 = 0; s0 < P; s0 += g.npl) {
         const int np = min(g.npl, P - s0);
         const int nrow = np * 3 * by;
+        {
+            // row kz of the octant is 6 * ntk contiguous entries (a multiple of 16 bytes); the pair of
+            // rank 0's self-mirror planes (kz = 0 and Mz/2) takes two rows, every other pair one
+            constexpr int n16 = 6 * ntk / 2;          // 16-byte chunks per row
+            const int npair = np >> 1;
+            const bool two0 = rk == 0 && s0 == 0;
+            const int nrows = npair + (two0 ? 1 : 0);
+            for (int i = t; i < nrows * n16; i += T) {
+                const int row = i / n16, c16 = i - row * n16;
+                int kz;
+                if (two0) kz = row == 0 ? 0 : (row == 1 ? Mz / 2 : slab_kz(rk, 2 * (row - 1), P, Mz));
+                else kz = slab_kz(rk, s0 + 2 * row, P, Mz);
+                const int kf = kz > Mz / 2 ? Mz - kz : kz;
+                cp_async16(gs + (int64_t)row * 6 * ntk + 2 * c16, Go + (int64_t)kf * 6 * ntk + 2 * c16);
+            }
+        }
         // x forward: rows (plane, component, y < by) of the slab into the workspace (natural kx)
         for (int task = t; task < nrow; task += T) {
             const int pc = task / by, y = task - pc * by;           // pc = plane * 3 + component
@@ -809,42 +853,36 @@ __device__ __forceinline__ void slab_planes(const InnerGroup<F>& g, F* sm, const
             for (int j = 0; j < HY; ++j) in[j] = j < by ? colp[j * wp] : czero<F>();
             fwd_half<LY>([&](int j) { return in[j]; }, [&](int k, F v) { colp[cbrev(k, LGY) * wp] = v; }, tw);
         }
+        cp_async_wait_all();                    // this thread's spectrum copies; the barrier publishes all
         __syncthreads();
-        // Green multiply: one octant entry per (pair of planes, kyf, kxf)
-        const int ntask = (np >> 1) * ntk;
+        // Green multiply: one task per (pair of planes, ky, kx); the point's octant entry (kyf, kxf) and
+        // the sign flips of its negative-half axes come from the staged rows
+        const int ntask = (np >> 1) * LY * LX;
         for (int task = t; task < ntask; task += T) {
-            const int pp = task / ntk, q = task - pp * ntk;
-            const int kyf = q / nkx, kxf = q - kyf * nkx;
+            const int kx = task & (LX - 1), r0 = task >> LGX;
+            const int ky = r0 & (LY - 1), pp = r0 >> LGY;
+            const int fx = kx > HX, fy = ky > HY;
+            const int q = (fy ? LY - ky : ky) * nkx + (fx ? LX - kx : kx);
             const int sa = s0 + 2 * pp;
             const int kza = slab_kz(rk, sa, P, Mz), kzb = slab_kz(rk, sa + 1, P, Mz);
             const int fza = kza > Mz / 2, fzb = kzb > Mz / 2;
-            const int kfa = fza ? Mz - kza : kza, kfb = fzb ? Mz - kzb : kzb;
+            const bool two0 = rk == 0 && s0 == 0;     // staged rows: see the prefetch above
+            const int rowa = two0 ? (pp == 0 ? 0 : pp + 1) : pp;
             F ga[6], gb[6];
-            const F* p0 = Go + ((int64_t)kfa * 6 * nky + kyf) * nkx + kxf;
+            const F* p0 = gs + rowa * 6 * ntk + q;
 #pragma unroll
             for (int c = 0; c < 6; ++c) ga[c] = p0[c * ntk];
-            if (kfb != kfa) {
-                const F* p1 = Go + ((int64_t)kfb * 6 * nky + kyf) * nkx + kxf;
+            if (two0 && pp == 0) {
+                const F* p1 = gs + 6 * ntk + q;        // rank 0's kz = Mz/2 row
 #pragma unroll
                 for (int c = 0; c < 6; ++c) gb[c] = p1[c * ntk];
             } else {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) gb[c] = ga[c];
             }
-            F* pa = ws + (2 * pp) * wpl;
-#pragma unroll
-            for (int ix = 0; ix < 2; ++ix) {
-                if (ix == 1 && (kxf == 0 || kxf == HX)) continue;
-                const int kx = ix ? LX - kxf : kxf;
-#pragma unroll
-                for (int iy = 0; iy < 2; ++iy) {
-                    if (iy == 1 && (kyf == 0 || kyf == HY)) continue;
-                    const int ky = iy ? LY - kyf : kyf;
-                    F* qa = pa + ky * wp + kx;
-                    green_pt(qa, cs, ga, ix, iy, fza);
-                    green_pt(qa + wpl, cs, gb, ix, iy, fzb);
-                }
-            }
+            F* qa = ws + (2 * pp) * wpl + ky * wp + kx;
+            green_pt(qa, cs, ga, fx, fy, fza);
+            green_pt(qa + wpl, cs, gb, fx, fy, fzb);
         }
         __syncthreads();
         // y inverse: columns, keep y < by
@@ -880,25 +918,20 @@ __device__ __forceinline__ void slab_planes(const InnerGroup<F>& g, F* sm, const
 // Inverse half: every box column of this rank gathers its kz values from their owners, inverse z
 // FFT, out = mask (in - u) with the iteration's inner products (OUT_V: <rhat, v>; OUT_T: <t, s>, <t, t>).
 template <int LZ, int OUT>
-__device__ __forceinline__ void slab_inv(const InnerGroup<F>& g, int64_t voff, const uint8_t* mask, F* sm,
+__device__ VIE_SLAB_INLINE void slab_inv(const InnerGroup<F>& g, int64_t voff, const uint8_t* mask, F* sm,
                                          const F* tw, F& a1, F& a2) {
     constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1, LG = ILog2<LZ>::v;
     const int bx = g.bx, by = g.by, bz = g.bz, plane = bx * by, ncol = 3 * plane;
-    const int rk = team_rank(), R = team_size(), P = LZ / R, bxp = g.bxp, zpl = 3 * by * bxp;
+    const int rk = team_rank(), R = team_size(), bxp = g.bxp;
     const FastDiv dbx = fd_of(g.fd_bx), dcol = fd_of(g.fd_col);
     const int64_t box = (int64_t)plane * bz;
     for (int col = rk * blockDim.x + threadIdx.x; col < ncol; col += R * blockDim.x) {
         const int comp = (int)fdiv(col, dcol), yx = col - comp * plane;
         const int y = (int)fdiv(yx, dbx), x = yx - y * bx;
-        F* src = sm + comp * by * bxp + y * bxp + x;
+        const int off = comp * by * bxp + y * bxp + x;
         F u[H];                                 // the stash of the FFT's upper half, then its output
-        inv_half<LZ>(
-            [&](int k) {
-                int r, sl;
-                slab_owner(cbrev(k, LG), P, LZ, r, sl);
-                return *rank_ptr(src + sl * zpl, r, R);
-            },
-            [&](int j, F v) { u[j] = v; }, [&](int j) { return u[j]; }, [&](int j, F v) { u[j] = v; }, tw);
+        inv_half<LZ>([&](int k) { return slab_tab[cbrev(k, LG)][off]; }, [&](int j, F v) { u[j] = v; },
+                     [&](int j) { return u[j]; }, [&](int j, F v) { u[j] = v; }, tw);
         const int64_t e0 = voff + comp * box + yx;
 #pragma unroll
         for (int j0 = 0; j0 < H; j0 += kSlabBatch) {
@@ -934,13 +967,15 @@ __device__ __forceinline__ void slab_inv(const InnerGroup<F>& g, int64_t voff, c
 }
 
 struct SlabMvm {
+    static constexpr int kUV = 4;
     template <int IN>
-    static __device__ __forceinline__ double2 fwd(const InnerGroup<F>& g, int64_t voff, F*, F*, const F* chi, F* sm,
-                                                  const F* tw, F c1, F c2, double2*) {
+    static __device__ __forceinline__ F fwd(const InnerGroup<F>& g, int64_t voff, F*, F*, const F* chi, F* sm,
+                                            const F* tw, F c1, F c2) {
         F acc = czero<F>();
+        slab_table(g, sm);
         VIE_LEN_SWITCH(g.lz, (acc = slab_fwd<LL, IN>(g, voff, chi, sm, tw, c1, c2)));
         team_sync();                            // every rank's kz planes complete
-        return make_double2(acc.x, acc.y);      // this thread's part of ||s||^2 (IN_S), summed later
+        return acc;                             // this thread's part of ||s||^2 (IN_S), summed later
     }
     static __device__ __forceinline__ void mid(const InnerGroup<F>& g, F*, F* sm, const F* tw) {
         switch (g.lx) {
@@ -950,16 +985,34 @@ struct SlabMvm {
         }
         team_sync();                            // every rank's planes back in its slab
     }
+    // the team sum that follows (its cluster barrier) also ends every read of the slabs
     template <int OUT>
     static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F*, F*, const uint8_t* mask, F* sm,
-                                               const F* tw, double2* red, double2& d1, double2& d2, double extra) {
-        F a1 = czero<F>(), a2 = czero<F>();
+                                               const F* tw, F& a1, F& a2) {
         VIE_LEN_SWITCH(g.lz, (slab_inv<LL, OUT>(g, voff, mask, sm, tw, a1, a2)));
-        d1 = make_double2(a1.x, a1.y);
-        d2 = make_double2(a2.x, extra);
-        team_sum2(d1, d2, red);                 // its cluster barrier also ends every read of the slabs
     }
 };
+
+// BiCGSTAB state of the block being solved, in shared memory: written by thread 0
+// inside team_sum (the FP64 scalar work of an iteration runs in that one thread)
+// and read by every thread after the sum's closing barrier.
+template <class C> struct BiState {
+    double2 rho, rho_prev, alpha, omega;
+    double tol2, bn2, res2, iters;
+    int status, half;
+    C cbeta, comega, calpha;                    // coefficients of the vector updates
+};
+
+// beta = (rho / rho_prev)(alpha / omega) for the next p update, or a breakdown.
+template <class C> __device__ __forceinline__ void next_beta(BiState<C>& S) {
+    if (!dgood(S.rho)) {
+        S.status = SEG_BREAKDOWN;
+        return;
+    }
+    const double2 beta = cmul(dcdiv(S.rho, S.rho_prev), dcdiv(S.alpha, S.omega));
+    S.cbeta = cmk<C>(beta.x, beta.y);
+    S.comega = cmk<C>(S.omega.x, S.omega.y);
+}
 
 template <class C, class Mvm>
 __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, double tol, int maxit, C* sm, const C* tw,
@@ -971,20 +1024,21 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
     C* W1 = g.w1 + (int64_t)b * 3 * g.bz * g.by * g.Mx;
     const C* chi = g.chi + (int64_t)b * box;
     const uint8_t* mask = g.mask + (int64_t)b * box;
+    __shared__ BiState<C> S;
 
     // x = 0, r = rhat = b, p = v = 0
     const int rk = team_rank(), nrk = team_size();
-    const int64_t first = (int64_t)rk * kUV * blockDim.x, step = (int64_t)nrk * kUV * blockDim.x;
+    const int64_t first = (int64_t)rk * Mvm::kUV * blockDim.x, step = (int64_t)nrk * Mvm::kUV * blockDim.x;
     C acc = czero<C>();
     for (int64_t i0 = first + threadIdx.x; i0 < n; i0 += step) {
-        C bv[kUV];
+        C bv[Mvm::kUV];
 #pragma unroll
-        for (int u = 0; u < kUV; ++u) {
+        for (int u = 0; u < Mvm::kUV; ++u) {
             const int64_t i = i0 + u * blockDim.x;
             if (i < n) bv[u] = g.b[voff + i];
         }
 #pragma unroll
-        for (int u = 0; u < kUV; ++u) {
+        for (int u = 0; u < Mvm::kUV; ++u) {
             const int64_t i = i0 + u * blockDim.x;
             if (i < n) {
                 const int64_t e = voff + i;
@@ -997,55 +1051,77 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
             }
         }
     }
-    double2 d1 = wide<C>(acc), d2 = make_double2(0, 0);
-    team_sum2(d1, d2, red);
-    const double bn2 = d1.x;
-    const double tol2 = tol * tol * bn2;
-    double2 rho = make_double2(bn2, 0.0), rho_prev = make_double2(1, 0), alpha = make_double2(1, 0),
-            omega = make_double2(1, 0);
-    double iters = 0.0, res2 = bn2;
-    int status = SEG_ACTIVE;
-    if (!(bn2 > 0.0) || !isfinite(bn2)) status = bn2 == 0.0 ? SEG_CONVERGED : SEG_BREAKDOWN;
-    for (int it = 0; it < maxit && status == SEG_ACTIVE; ++it) {
-        if (!dgood(rho)) { status = SEG_BREAKDOWN; break; }
-        double2 beta = cmul(dcdiv(rho, rho_prev), dcdiv(alpha, omega));
+    team_sum(acc, czero<C>(), red, [&](double2 sa, double2) {
+        const double bn2 = sa.x;
+        S.bn2 = bn2;
+        S.tol2 = tol * tol * bn2;
+        S.rho = make_double2(bn2, 0.0);
+        S.rho_prev = S.alpha = S.omega = make_double2(1, 0);
+        S.iters = 0.0;
+        S.res2 = bn2;
+        S.half = 0;
+        S.status = SEG_ACTIVE;
+        if (!(bn2 > 0.0) || !isfinite(bn2)) S.status = bn2 == 0.0 ? SEG_CONVERGED : SEG_BREAKDOWN;
+        else next_beta(S);
+    });
+    for (int it = 0; it < maxit && S.status == SEG_ACTIVE; ++it) {
         // v = A p, p = r + beta (p - omega v)
-        Mvm::template fwd<IN_P>(g, voff, W1, W, chi, sm, tw, cmk<C>(beta.x, beta.y), cmk<C>(omega.x, omega.y), red);
+        Mvm::template fwd<IN_P>(g, voff, W1, W, chi, sm, tw, S.cbeta, S.comega);
         Mvm::mid(g, W, sm, tw);
         if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm);
-        double2 sigma, unused;
-        Mvm::template inv<OUT_V>(g, voff, W1, W, mask, sm, tw, red, sigma, unused, 0.0);
-        if (!dgood(sigma)) { status = SEG_BREAKDOWN; break; }
-        alpha = dcdiv(rho, sigma);
+        C p1 = czero<C>(), p2 = czero<C>();
+        Mvm::template inv<OUT_V>(g, voff, W1, W, mask, sm, tw, p1, p2);
+        team_sum(p1, p2, red, [&](double2 sigma, double2) {
+            if (!dgood(sigma)) {
+                S.status = SEG_BREAKDOWN;
+                return;
+            }
+            S.alpha = dcdiv(S.rho, sigma);
+            S.calpha = cmk<C>(S.alpha.x, S.alpha.y);
+        });
+        if (S.status != SEG_ACTIVE) break;
         // s = r - alpha v and t = A s; ||s||^2 is summed together with <t,s> and <t,t>, so the
         // half-step test (same value, same decision) costs no reduction of its own
-        double2 snp = Mvm::template fwd<IN_S>(g, voff, W1, W, chi, sm, tw, cmk<C>(alpha.x, alpha.y), czero<C>(), red);
+        const C snp = Mvm::template fwd<IN_S>(g, voff, W1, W, chi, sm, tw, S.calpha, czero<C>());
         Mvm::mid(g, W, sm, tw);
         if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm + g.kb_upd);
-        double2 ts, tt;
-        Mvm::template inv<OUT_T>(g, voff, W1, W, mask, sm, tw, red, ts, tt, snp.x);
-        const double sn2 = tt.y;
-        if (sn2 <= tol2) {
+        p1 = czero<C>();
+        p2 = czero<C>();
+        Mvm::template inv<OUT_T>(g, voff, W1, W, mask, sm, tw, p1, p2);
+        p2.y = snp.x;                           // the deferred ||s||^2 rides in the unused slot
+        team_sum(p1, p2, red, [&](double2 ts, double2 tt) {
+            const double sn2 = tt.y;
+            if (sn2 <= S.tol2) {
+                S.half = 1;
+                S.res2 = sn2;
+                S.iters += 0.5;
+                S.status = SEG_CONVERGED;
+                return;
+            }
+            if (!(tt.x > 0.0) || !isfinite(tt.x)) {
+                S.status = SEG_BREAKDOWN;
+                return;
+            }
+            S.omega = make_double2(ts.x / tt.x, ts.y / tt.x);
+            S.comega = cmk<C>(S.omega.x, S.omega.y);
+        });
+        if (S.half) {
             // half-step convergence: x += alpha p (t is not needed)
-            C ac = cmk<C>(alpha.x, alpha.y);
+            const C ac = S.calpha;
             for (int64_t i = (int64_t)rk * blockDim.x + threadIdx.x; i < n; i += (int64_t)nrk * blockDim.x) {
                 int64_t e = voff + i;
                 g.x[e] = g.x[e] + cmul(ac, g.p[e]);
             }
-            iters += 0.5;
-            res2 = sn2;
-            status = SEG_CONVERGED;
             break;
         }
-        if (!(tt.x > 0.0) || !isfinite(tt.x)) { status = SEG_BREAKDOWN; break; }
-        omega = make_double2(ts.x / tt.x, ts.y / tt.x);
+        if (S.status != SEG_ACTIVE) break;
         // x += alpha p + omega s, r = s - omega t; rho = <rhat, r>, ||r||^2
-        C ac = cmk<C>(alpha.x, alpha.y), oc = cmk<C>(omega.x, omega.y);
+        const C ac = S.calpha, oc = S.comega;
         C a1 = czero<C>(), a2 = czero<C>();
         for (int64_t i0 = first + threadIdx.x; i0 < n; i0 += step) {
-            C sv[kUV], xv[kUV], pv[kUV], tv[kUV], hv[kUV];
+            C sv[Mvm::kUV], xv[Mvm::kUV], pv[Mvm::kUV], tv[Mvm::kUV], hv[Mvm::kUV];
 #pragma unroll
-            for (int u = 0; u < kUV; ++u) {
+            for (int u = 0; u < Mvm::kUV; ++u) {
                 const int64_t i = i0 + u * blockDim.x;
                 if (i < n) {
                     const int64_t e = voff + i;
@@ -1057,7 +1133,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kUV; ++u) {
+            for (int u = 0; u < Mvm::kUV; ++u) {
                 const int64_t i = i0 + u * blockDim.x;
                 if (i < n) {
                     const int64_t e = voff + i;
@@ -1069,25 +1145,24 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
                 }
             }
         }
-        d1 = wide<C>(a1);
-        d2 = wide<C>(a2);
-        team_sum2(d1, d2, red);
-        rho_prev = rho;
-        rho = d1;
-        res2 = d2.x;
-        iters += 1.0;
-        if (!isfinite(res2)) { status = SEG_BREAKDOWN; break; }
-        if (res2 <= tol2) { status = SEG_CONVERGED; break; }
-        if (omega.x == 0.0 && omega.y == 0.0) { status = SEG_BREAKDOWN; break; }
+        team_sum(a1, a2, red, [&](double2 r1, double2 r2) {
+            S.rho_prev = S.rho;
+            S.rho = r1;
+            S.res2 = r2.x;
+            S.iters += 1.0;
+            if (!isfinite(S.res2)) S.status = SEG_BREAKDOWN;
+            else if (S.res2 <= S.tol2) S.status = SEG_CONVERGED;
+            else if (S.omega.x == 0.0 && S.omega.y == 0.0) S.status = SEG_BREAKDOWN;
+            else next_beta(S);
+        });
     }
-    if (status == SEG_ACTIVE) status = SEG_MAXIT;
     if (rk == 0 && threadIdx.x == 0) {
-        SegState& S = g.st[b];
-        S.bnorm2 = bn2;
-        S.res2 = res2;
-        S.iters = iters;
-        S.status = status;
-        S.maxit = maxit;
+        SegState& St = g.st[b];
+        St.bnorm2 = S.bn2;
+        St.res2 = S.res2;
+        St.iters = S.iters;
+        St.status = S.status == SEG_ACTIVE ? SEG_MAXIT : S.status;
+        St.maxit = maxit;
     }
     __syncthreads();
 }
@@ -1117,7 +1192,7 @@ __global__ void __launch_bounds__(SLAB ? kSlabThreads : kInnerThreads, SLAB ? 1 
             int* units, int npl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
-    __shared__ double2 red[2 * (kInnerThreads / 32)];
+    __shared__ double2 red[2 * ((SLAB ? kSlabThreads : kInnerThreads) / 32)];   // two sums per warp
     __shared__ int item;
     cg::cluster_group cl = cg::this_cluster();
     if (threadIdx.x == 0) team_slot = 0;
@@ -1166,7 +1241,7 @@ int inner_cluster_forced() {
 bool slab_disabled() {
     static const bool r = [] {
         const char* e = getenv("VIE_INNER_SLAB");
-        return e == nullptr || atoi(e) == 0;
+        return e != nullptr && atoi(e) == 0;
     }();
     return r;
 }
@@ -1218,7 +1293,8 @@ static size_t slab_smem(const BoxSet& bs, int R, int npl) {
     const size_t bxp = (size_t)(bs.bx | 1);
     const size_t zb = (size_t)(bs.Mz / R) * 3 * bs.by * bxp;
     const size_t ws = (size_t)npl * 3 * bs.My * (bs.Mx + 1);
-    return (zb + ws) * sizeof(float2);
+    const size_t gs = (size_t)(npl / 2 + 1) * 6 * (bs.Mx / 2 + 1) * (bs.My / 2 + 1);   // staged spectrum rows
+    return ((size_t)slab_gs_offset((int)(zb + ws)) + gs) * sizeof(float2);
 }
 // Smallest cluster size (1, 2 or 4) whose slab fits, or 0.
 static int slab_min_ranks(const BoxSet& bs) {
@@ -1244,7 +1320,7 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
     size_t smem = 0;
     int64_t bytes_per_block = 0;
     bool any_slab = false;
-    int rmin_slab = 1;
+    int rmin_slab = 1, rmax_slab = 8;
     std::vector<const BoxSet*> slab_sets;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const InnerJob<C>& j = jobs[i];
@@ -1275,6 +1351,7 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         if (g.slab) {
             any_slab = true;
             rmin_slab = std::max(rmin_slab, slab_min_ranks(bs));
+            rmax_slab = std::min(rmax_slab, bs.Mz / 2);
             slab_sets.push_back(&bs);
         }
         if (g.reg) sm = reg_smem(bs);
@@ -1308,7 +1385,7 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
     };
     // one block per cluster of R CTAs; as many clusters as fit at once, pulling blocks from the queue
     auto launch = [&](const int2* work, int n, int* next, int R, cudaStream_t st, int* units) -> int {
-        if (any_slab) R = std::max(R, rmin_slab);
+        if (any_slab) R = std::min(std::max(R, rmin_slab), rmax_slab);   // every rank holds >= 2 kz planes
         int npl = 2;
         const size_t sm_bytes = launch_smem(R, &npl);
         // opt in to the exact dynamic size: the default 48 KB limit also counts the static shared memory

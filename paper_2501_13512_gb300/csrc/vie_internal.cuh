@@ -338,7 +338,8 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
                      int* d_next, double tol, int maxit, cudaStream_t s, int cluster = 0,
                      const InnerSplit* split = nullptr);
 int inner_cluster_forced();
-// True when the environment variable VIE_INNER_SLAB is 0: complex64 blocks keep the register-FFT MVM.
+// True when the environment variable VIE_INNER_SLAB is 0: complex64 blocks keep the register-FFT MVM
+// instead of the slab MVM (read once).
 bool slab_disabled();
 template <class C> inline const C* tw_of(const Twiddles& t);
 template <> inline const double2* tw_of<double2>(const Twiddles& t) { return t.d128; }
