@@ -96,54 +96,69 @@ template <class T> __device__ __forceinline__ T shfl_dn(T v, int o) { return __s
 // computes identical sums. Two rank slots alternate between consecutive sums: a
 // slot is rewritten two sums later, after every rank has passed the cluster
 // barrier of the sum in between, so one cluster barrier per sum suffices.
-template <class C, class Fn>
-__device__ __forceinline__ void team_sum(C a, C b, double2* red, Fn fn) {
+constexpr int kTeamSumMax = 4;                 // complex values one team sum carries
+
+template <int N, class C, class Fn>
+__device__ __forceinline__ void team_sum_n(C (&v)[N], double2* red, Fn fn) {
+    static_assert(N <= kTeamSumMax, "team_sum_n: too many values");
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a.x += shfl_dn(a.x, o);
-        a.y += shfl_dn(a.y, o);
-        b.x += shfl_dn(b.x, o);
-        b.y += shfl_dn(b.y, o);
-    }
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            v[i].x += shfl_dn(v[i].x, o);
+            v[i].y += shfl_dn(v[i].y, o);
+        }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0) {
-        red[2 * w] = make_double2(a.x, a.y);
-        red[2 * w + 1] = make_double2(b.x, b.y);
-    }
+    if (l == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[N * w + i] = make_double2(v[i].x, v[i].y);
     __syncthreads();
     cg::cluster_group cl = cg::this_cluster();
     const unsigned R = cl.num_blocks();
-    __shared__ double2 xred[2][2];
-    double2 sa = make_double2(0, 0), sb = make_double2(0, 0);
+    __shared__ double2 xred[2][kTeamSumMax];
+    double2 sum[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) sum[i] = make_double2(0, 0);
     if (threadIdx.x == 0) {
-        for (int i = 0; i < nw; ++i) {
-            sa.x += red[2 * i].x; sa.y += red[2 * i].y;
-            sb.x += red[2 * i + 1].x; sb.y += red[2 * i + 1].y;
-        }
+        for (int k = 0; k < nw; ++k)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                sum[i].x += red[N * k + i].x;
+                sum[i].y += red[N * k + i].y;
+            }
         if (R > 1) {
             team_slot ^= 1;
-            xred[team_slot][0] = sa;
-            xred[team_slot][1] = sb;
+#pragma unroll
+            for (int i = 0; i < N; ++i) xred[team_slot][i] = sum[i];
         }
     }
     if (R > 1) {
         cl.sync();
         if (threadIdx.x == 0) {
-            sa = make_double2(0, 0);
-            sb = make_double2(0, 0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) sum[i] = make_double2(0, 0);
             for (unsigned r = 0; r < R; ++r) {
                 const double2* q = cl.map_shared_rank(&xred[team_slot][0], r);
-                sa.x += q[0].x; sa.y += q[0].y;
-                sb.x += q[1].x; sb.y += q[1].y;
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    sum[i].x += q[i].x;
+                    sum[i].y += q[i].y;
+                }
             }
         }
     }
-    if (threadIdx.x == 0) fn(sa, sb);
+    if (threadIdx.x == 0) fn(sum);
     __syncthreads();
 }
 
-enum { IN_P = 0, IN_S = 1 };
-enum { OUT_V = 0, OUT_T = 1 };
+template <class C, class Fn>
+__device__ __forceinline__ void team_sum(C a, C b, double2* red, Fn fn) {
+    C v[2] = {a, b};
+    team_sum_n<2>(v, red, [&](const double2 (&s)[2]) { fn(s[0], s[1]); });
+}
+
+enum { IN_P = 0, IN_S = 1, IN_PX = 2 };   // IN_PX: p update with the previous step's x and r updates fused
+enum { OUT_V = 0, OUT_T = 1, OUT_TX = 2 };   // OUT_TX: OUT_T with <rhat, s> and <rhat, t> as well
 
 // Phase XY: plane tiles, fused vector update + chi, 2D forward FFT, store spectrum.
 // IN_P: p = r + beta (p - omega v);  IN_S: s = r - alpha v (returns ||s||^2 in .x).
@@ -598,6 +613,7 @@ __device__ __forceinline__ void x_inv_reg(const InnerGroup<F>& g, int64_t voff, 
 // The two MVM implementations used by solve_block.
 template <class C> struct SmemMvm {
     static constexpr int kUV = 1;       // elements per thread per batch in the block-vector passes
+    static constexpr bool kMerged = false;
     template <int IN>
     static __device__ C fwd(const InnerGroup<C>& g, int64_t voff, C* W1, C* W2, const C* chi, C* sm, const C* tw,
                             C c1, C c2) {
@@ -619,6 +635,7 @@ template <class C> struct SmemMvm {
 
 struct RegMvm {
     static constexpr int kUV = 1;
+    static constexpr bool kMerged = false;
     template <int IN>
     static __device__ __forceinline__ F fwd(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const F* chi, F* sm,
                                             const F* tw, F c1, F c2) {
@@ -727,11 +744,12 @@ __device__ __forceinline__ void slab_table(const InnerGroup<F>& g, F* sm) {
     __syncthreads();
 }
 
-// Forward half of the slab MVM: update (IN_P: p = r + c1 (p - c2 v); IN_S: s = r - c1 v), w = chi in,
-// z FFT of every box column of this rank, kz values stored into their owners' slabs.
+// Forward half of the slab MVM: update (IN_P: p = r + c1 (p - c2 v); IN_S: s = r - c1 v; IN_PX: the
+// previous step's r = s - c2 t and x += c3 p + c2 s, then p = r + c1 (p - c2 v)), w = chi in, z FFT of
+// every box column of this rank, kz values stored into their owners' slabs.
 template <int LZ, int IN>
 __device__ VIE_SLAB_INLINE F slab_fwd(const InnerGroup<F>& g, int64_t voff, const F* chi, F* sm, const F* tw, F c1,
-                                      F c2) {
+                                      F c2, F c3) {
     constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1, LG = ILog2<LZ>::v;
     const int bx = g.bx, by = g.by, bz = g.bz, plane = bx * by, ncol = 3 * plane;
     const int rk = team_rank(), R = team_size(), bxp = g.bxp;
@@ -745,15 +763,19 @@ __device__ VIE_SLAB_INLINE F slab_fwd(const InnerGroup<F>& g, int64_t voff, cons
         F a[H];
 #pragma unroll
         for (int j0 = 0; j0 < H; j0 += kSlabBatch) {
-            F ra[kSlabBatch], pa[kSlabBatch], va[kSlabBatch], ca[kSlabBatch];
+            F ra[kSlabBatch], pa[kSlabBatch], va[kSlabBatch], ca[kSlabBatch], xa[kSlabBatch], ta[kSlabBatch];
 #pragma unroll
             for (int u = 0; u < kSlabBatch; ++u) {       // every load of the batch first
                 const int j = j0 + u;
                 if (j < H && j < bz) {
                     const int64_t e = e0 + (int64_t)j * plane;
-                    ra[u] = g.r[e];
+                    ra[u] = IN == IN_PX ? g.s[e] : g.r[e];
                     va[u] = g.v[e];
-                    if (IN == IN_P) pa[u] = g.p[e];
+                    if (IN != IN_S) pa[u] = g.p[e];
+                    if (IN == IN_PX) {
+                        ta[u] = g.t[e];
+                        xa[u] = g.x[e];
+                    }
                     ca[u] = chi[j * plane + yx];
                 }
             }
@@ -765,7 +787,13 @@ __device__ VIE_SLAB_INLINE F slab_fwd(const InnerGroup<F>& g, int64_t voff, cons
                 if (j < bz) {
                     const int64_t e = e0 + (int64_t)j * plane;
                     F in;
-                    if (IN == IN_P) {
+                    if (IN == IN_PX) {
+                        const F rr = ra[u] - cmul(c2, ta[u]);
+                        g.r[e] = rr;
+                        g.x[e] = xa[u] + cmul(c3, pa[u]) + cmul(c2, ra[u]);
+                        in = rr + cmul(c1, pa[u] - cmul(c2, va[u]));
+                        g.p[e] = in;
+                    } else if (IN == IN_P) {
                         in = ra[u] + cmul(c1, pa[u] - cmul(c2, va[u]));
                         g.p[e] = in;
                     } else {
@@ -916,10 +944,11 @@ __device__ VIE_SLAB_INLINE void slab_planes(const InnerGroup<F>& g, F* sm, const
 }
 
 // Inverse half: every box column of this rank gathers its kz values from their owners, inverse z
-// FFT, out = mask (in - u) with the iteration's inner products (OUT_V: <rhat, v>; OUT_T: <t, s>, <t, t>).
+// FFT, out = mask (in - u) with the iteration's inner products (OUT_V: <rhat, v>; OUT_T: <t, s>,
+// <t, t>; OUT_TX: those and <rhat, s>, <rhat, t>) accumulated into acc[0..3].
 template <int LZ, int OUT>
 __device__ VIE_SLAB_INLINE void slab_inv(const InnerGroup<F>& g, int64_t voff, const uint8_t* mask, F* sm,
-                                         const F* tw, F& a1, F& a2) {
+                                         const F* tw, F (&acc)[4]) {
     constexpr int H = LZ / 2 > 0 ? LZ / 2 : 1, LG = ILog2<LZ>::v;
     const int bx = g.bx, by = g.by, bz = g.bz, plane = bx * by, ncol = 3 * plane;
     const int rk = team_rank(), R = team_size(), bxp = g.bxp;
@@ -943,7 +972,7 @@ __device__ VIE_SLAB_INLINE void slab_inv(const InnerGroup<F>& g, int64_t voff, c
                 if (j < H && j < bz) {
                     const int64_t e = e0 + (int64_t)j * plane;
                     ia[q] = OUT == OUT_V ? g.p[e] : g.s[e];
-                    if (OUT == OUT_V) ha[q] = g.rhat[e];
+                    if (OUT != OUT_T) ha[q] = g.rhat[e];
                     ma[q] = mask[j * plane + yx];
                 }
             }
@@ -955,11 +984,15 @@ __device__ VIE_SLAB_INLINE void slab_inv(const InnerGroup<F>& g, int64_t voff, c
                 const F o = ma[q] ? ia[q] - u[j] : czero<F>();
                 if (OUT == OUT_V) {
                     g.v[e] = o;
-                    acc_dot(a1, ha[q], o);
+                    acc_dot(acc[0], ha[q], o);
                 } else {
                     g.t[e] = o;
-                    acc_dot(a1, o, ia[q]);
-                    a2.x += o.x * o.x + o.y * o.y;
+                    acc_dot(acc[0], o, ia[q]);
+                    acc[1].x += o.x * o.x + o.y * o.y;
+                    if (OUT == OUT_TX) {
+                        acc_dot(acc[2], ha[q], ia[q]);
+                        acc_dot(acc[3], ha[q], o);
+                    }
                 }
             }
         }
@@ -968,12 +1001,13 @@ __device__ VIE_SLAB_INLINE void slab_inv(const InnerGroup<F>& g, int64_t voff, c
 
 struct SlabMvm {
     static constexpr int kUV = 4;
+    static constexpr bool kMerged = true;       // the x/r update rides in the next p update (IN_PX, OUT_TX)
     template <int IN>
     static __device__ __forceinline__ F fwd(const InnerGroup<F>& g, int64_t voff, F*, F*, const F* chi, F* sm,
-                                            const F* tw, F c1, F c2) {
+                                            const F* tw, F c1, F c2, F c3 = czero<F>()) {
         F acc = czero<F>();
         slab_table(g, sm);
-        VIE_LEN_SWITCH(g.lz, (acc = slab_fwd<LL, IN>(g, voff, chi, sm, tw, c1, c2)));
+        VIE_LEN_SWITCH(g.lz, (acc = slab_fwd<LL, IN>(g, voff, chi, sm, tw, c1, c2, c3)));
         team_sync();                            // every rank's kz planes complete
         return acc;                             // this thread's part of ||s||^2 (IN_S), summed later
     }
@@ -988,8 +1022,16 @@ struct SlabMvm {
     // the team sum that follows (its cluster barrier) also ends every read of the slabs
     template <int OUT>
     static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F*, F*, const uint8_t* mask, F* sm,
-                                               const F* tw, F& a1, F& a2) {
-        VIE_LEN_SWITCH(g.lz, (slab_inv<LL, OUT>(g, voff, mask, sm, tw, a1, a2)));
+                                               const F* tw, F (&acc)[4]) {
+        VIE_LEN_SWITCH(g.lz, (slab_inv<LL, OUT>(g, voff, mask, sm, tw, acc)));
+    }
+    template <int OUT>
+    static __device__ __forceinline__ void inv(const InnerGroup<F>& g, int64_t voff, F* W1, F* W2, const uint8_t* mask,
+                                               F* sm, const F* tw, F& a1, F& a2) {
+        F acc[4] = {a1, a2, czero<F>(), czero<F>()};
+        inv<OUT>(g, voff, W1, W2, mask, sm, tw, acc);
+        a1 = acc[0];
+        a2 = acc[1];
     }
 };
 
@@ -1000,6 +1042,7 @@ template <class C> struct BiState {
     double2 rho, rho_prev, alpha, omega;
     double tol2, bn2, res2, iters;
     int status, half;
+    int pend;                                   // merged form: the last full step's x update is pending
     C cbeta, comega, calpha;                    // coefficients of the vector updates
 };
 
@@ -1060,10 +1103,83 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
         S.iters = 0.0;
         S.res2 = bn2;
         S.half = 0;
+        S.pend = 0;
         S.status = SEG_ACTIVE;
         if (!(bn2 > 0.0) || !isfinite(bn2)) S.status = bn2 == 0.0 ? SEG_CONVERGED : SEG_BREAKDOWN;
         else next_beta(S);
     });
+    if constexpr (Mvm::kMerged) {
+        // One pass and one sum fewer per iteration: r = s - omega t and x += alpha p + omega s are
+        // applied in the next p update (IN_PX), and <rhat, r> = <rhat, s> - omega <rhat, t> and
+        // ||r||^2 = ||s||^2 - |<t, s>|^2 / ||t||^2 come from the sums of the t pass (OUT_TX).
+        for (int it = 0; it < maxit && S.status == SEG_ACTIVE; ++it) {
+            if (it == 0) Mvm::template fwd<IN_P>(g, voff, W1, W, chi, sm, tw, S.cbeta, S.comega);
+            else Mvm::template fwd<IN_PX>(g, voff, W1, W, chi, sm, tw, S.cbeta, S.comega, S.calpha);
+            Mvm::mid(g, W, sm, tw);
+            if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm);
+            C p1 = czero<C>(), p2 = czero<C>();
+            Mvm::template inv<OUT_V>(g, voff, W1, W, mask, sm, tw, p1, p2);
+            team_sum(p1, p2, red, [&](double2 sigma, double2) {
+                S.pend = 0;                     // the p update took the previous step's x update
+                if (!dgood(sigma)) {
+                    S.status = SEG_BREAKDOWN;
+                    return;
+                }
+                S.alpha = dcdiv(S.rho, sigma);
+                S.calpha = cmk<C>(S.alpha.x, S.alpha.y);
+            });
+            if (S.status != SEG_ACTIVE) break;
+            const C snp = Mvm::template fwd<IN_S>(g, voff, W1, W, chi, sm, tw, S.calpha, czero<C>());
+            Mvm::mid(g, W, sm, tw);
+            if (units != nullptr && rk == 0 && threadIdx.x == 0) atomicAdd(units, g.kb_mvm);
+            C q4[4] = {czero<C>(), czero<C>(), czero<C>(), czero<C>()};
+            Mvm::template inv<OUT_TX>(g, voff, W1, W, mask, sm, tw, q4);
+            q4[1].y = snp.x;                    // the deferred ||s||^2 rides in the unused slot
+            team_sum_n<4>(q4, red, [&](const double2 (&q)[4]) {
+                const double2 ts = q[0], rs = q[2], rt = q[3];
+                const double tt = q[1].x, sn2 = q[1].y;
+                if (sn2 <= S.tol2) {
+                    S.half = 1;
+                    S.res2 = sn2;
+                    S.iters += 0.5;
+                    S.status = SEG_CONVERGED;
+                    return;
+                }
+                if (!(tt > 0.0) || !isfinite(tt)) {
+                    S.status = SEG_BREAKDOWN;
+                    return;
+                }
+                S.omega = make_double2(ts.x / tt, ts.y / tt);
+                S.comega = cmk<C>(S.omega.x, S.omega.y);
+                S.pend = 1;
+                S.rho_prev = S.rho;
+                S.rho = make_double2(rs.x - (S.omega.x * rt.x - S.omega.y * rt.y),
+                                     rs.y - (S.omega.x * rt.y + S.omega.y * rt.x));
+                S.res2 = fmax(sn2 - (ts.x * ts.x + ts.y * ts.y) / tt, 0.0);
+                S.iters += 1.0;
+                if (!isfinite(S.res2)) S.status = SEG_BREAKDOWN;
+                else if (S.res2 <= S.tol2) S.status = SEG_CONVERGED;
+                else if (S.omega.x == 0.0 && S.omega.y == 0.0) S.status = SEG_BREAKDOWN;
+                else next_beta(S);
+            });
+            if (S.half) {
+                const C ac = S.calpha;          // half-step convergence: x += alpha p
+                for (int64_t i = (int64_t)rk * blockDim.x + threadIdx.x; i < n; i += (int64_t)nrk * blockDim.x) {
+                    int64_t e = voff + i;
+                    g.x[e] = g.x[e] + cmul(ac, g.p[e]);
+                }
+                break;
+            }
+        }
+        if (S.pend) {
+            // the last full step's x update (no p update followed it)
+            const C ac = S.calpha, oc = S.comega;
+            for (int64_t i = (int64_t)rk * blockDim.x + threadIdx.x; i < n; i += (int64_t)nrk * blockDim.x) {
+                int64_t e = voff + i;
+                g.x[e] = g.x[e] + cmul(ac, g.p[e]) + cmul(oc, g.s[e]);
+            }
+        }
+    } else {
     for (int it = 0; it < maxit && S.status == SEG_ACTIVE; ++it) {
         // v = A p, p = r + beta (p - omega v)
         Mvm::template fwd<IN_P>(g, voff, W1, W, chi, sm, tw, S.cbeta, S.comega);
@@ -1156,6 +1272,7 @@ __device__ __forceinline__ void solve_block(const InnerGroup<C>& g, int b, doubl
             else next_beta(S);
         });
     }
+    }
     if (rk == 0 && threadIdx.x == 0) {
         SegState& St = g.st[b];
         St.bnorm2 = S.bn2;
@@ -1192,7 +1309,7 @@ __global__ void __launch_bounds__(SLAB ? kSlabThreads : kInnerThreads, SLAB ? 1 
             int* units, int npl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
-    __shared__ double2 red[2 * ((SLAB ? kSlabThreads : kInnerThreads) / 32)];   // two sums per warp
+    __shared__ double2 red[kTeamSumMax * ((SLAB ? kSlabThreads : kInnerThreads) / 32)];   // per-warp sums
     __shared__ int item;
     cg::cluster_group cl = cg::this_cluster();
     if (threadIdx.x == 0) team_slot = 0;
@@ -1361,7 +1478,8 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
         const int64_t es = sizeof(C), box = bs.box_elems();
         const int64_t w2b = 3LL * bs.bz * bs.My * bs.Mx * es;
         const int64_t w1b = 3LL * bs.bz * bs.by * bs.Mx * es;
-        const int64_t mvm = g.slab ? 6LL * bs.oct_elems() * es + box * (es + 1) + 7 * 3 * box * es
+        // slab (merged BiCGSTAB): an iteration's two MVMs and fused passes move 17 box vectors
+        const int64_t mvm = g.slab ? 6LL * bs.oct_elems() * es + box * (es + 1) + 17 * 3 * box * es / 2
                             : g.reg ? 4 * w1b + 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 7 * 3 * box * es
                                     : 4 * w2b + 6LL * bs.spec_elems() * es + box * (es + 1) + 4 * 3 * box * es;
         g.kb_mvm = (int)((mvm + 1023) / 1024);
