@@ -414,7 +414,8 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
         std::vector<std::pair<int64_t, int2>> items;
         int job = 0;
         // AUTO: every group whose plane fits joins one persistent launch when the
-        // fitting groups hold at least kInnerMinBlocks blocks in total
+        // fitting groups hold at least kInnerMinBlocks blocks in total (fewer, larger
+        // blocks iterate faster in the batched launches, which use the whole GPU per step)
         int fit_blocks = 0;
         for (auto& gr : g->groups)
             if (inner_persistent_ok(gr.bs, es, true)) fit_blocks += gr.bs.nb;
@@ -689,17 +690,26 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     const int tried = g->tune_count[pi];
     const bool tuning = !jobs.empty() && tried < 3 && !inner_cluster_forced();
     const int choice = tuning ? (slab ? kCandSlab : kCand)[tried] : (g->tune_best[pi] ? g->tune_best[pi] : 2);
+    // with batched groups as well, the persistent launch runs on the grid's second stream beside
+    // the batched steps (no split launch then)
+    const bool beside = !jobs.empty() && !batched.empty();
     InnerSplit split;
-    split.nheavy = choice == -1 ? g->nheavy[pi] : 0;
+    split.nheavy = choice == -1 && !beside ? g->nheavy[pi] : 0;
     split.cluster = slab ? 2 : 4;
     split.s2 = g->s2;
     split.fork = g->fork_ev;
     split.join = g->join_ev;
-    if (tuning) VIE_CK(cudaEventRecord(g->tev[0], s));
+    cudaStream_t sp_stream = s;
+    if (beside) {
+        VIE_CK(cudaEventRecord(g->fork_ev, s));
+        VIE_CK(cudaStreamWaitEvent(g->s2, g->fork_ev, 0));
+        sp_stream = g->s2;
+    }
+    if (tuning) VIE_CK(cudaEventRecord(g->tev[0], sp_stream));
     VIE_TRY(inner_persistent<C>(jobs, c128 ? g->work128 : g->work64, c128 ? g->nwork128 : g->nwork64,
-                                g->inner_groups, g->inner_next, tol, maxit, s,
+                                g->inner_groups, g->inner_next, tol, maxit, sp_stream,
                                 choice == -1 ? (slab ? 1 : 2) : choice, &split));
-    if (tuning) VIE_CK(cudaEventRecord(g->tev[1], s));
+    if (tuning) VIE_CK(cudaEventRecord(g->tev[1], sp_stream));
     std::vector<Bicg<C>> bk(ng);
     for (int i : batched) {
         Group& gr = g->groups[i];
@@ -738,6 +748,10 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             for (int i : batched) active += ring[prev * (ng + 1) + i];
             if (active == 0) break;
         }
+    }
+    if (beside) {
+        VIE_CK(cudaEventRecord(g->join_ev, g->s2));
+        VIE_CK(cudaStreamWaitEvent(s, g->join_ev, 0));
     }
     VIE_TRY(precond_copy_unblocked<C>(g, b, y, s));
     for (int i = 0; i < ng; ++i) VIE_TRY(precond_scatter_group<C>(g, g->groups[i], group_vecs<C>(g->groups[i]).x, y, s));
