@@ -79,6 +79,11 @@ typedef struct {
                                 block (identity); any non-negative ids; NULL = all
                                 -1; copied                                           */
     uint32_t flags;          /* 0 or one VIE_GRID_INNER_* value                      */
+    int32_t block_expand;    /* E in [0, 64]: each block is solved on its voxels plus
+                                every voxel with chi != 0 within Chebyshev distance E,
+                                and only its own voxels are kept (expanded blocks,
+                                restricted additive Schwarz; 0 = the blocks of
+                                Eq. 10 as given)                                     */
 } vie_grid_desc;
 
 /* How the inner block solves of the preconditioner run (vie_grid_desc.flags).
@@ -134,6 +139,19 @@ int vie_grid_get_info(const vie_grid* grid, vie_grid_info* info);
  * Errors: VIE_EINVAL, VIE_ENOMEM, VIE_ECUDA. */
 int vie_green_spectrum(vie_grid* grid, double k0, int precision_mask,
                        vie_stream_t stream, vie_spectrum** out);
+
+/* As vie_green_spectrum, with cube-integrated near-neighbour entries: for lattice
+ * offsets D with 0 < max(|Dx|, |Dy|, |Dz|) <= near_radius, K(D) is the mean of
+ * k0^2 G over the source voxel (the cube of side h centred at D h) times h^3,
+ * by a tensor Gauss-Legendre rule of near_order points per axis, instead of
+ * k0^2 G(D h) h^3 at the voxel centre. The paper does not say how it integrates
+ * near couplings (Section II.A); this is an accuracy variant of the same
+ * Toeplitz operator, used by every MVM and block solve with this spectrum.
+ * near_radius 0 gives vie_green_spectrum. Errors: VIE_EINVAL (near_radius
+ * outside [0, 8], near_order outside [1, 16] when near_radius > 0), as
+ * vie_green_spectrum otherwise. */
+int vie_green_spectrum_near(vie_grid* grid, double k0, int precision_mask, int32_t near_radius,
+                            int32_t near_order, vie_stream_t stream, vie_spectrum** out);
 
 /* Waits for the device, then frees the spectra. Errors: VIE_EINVAL. */
 int vie_spectrum_release(vie_spectrum* spectrum);

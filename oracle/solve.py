@@ -35,13 +35,14 @@ def plane_wave(n, h, k, khat, pol):
 
 
 def solve(eps_r, block_id, h, k, einc, tol=1e-6, use_precond=True,
-          inner_tol=1e-2, inner_maxit=1000, maxit=1000, near=None):
+          inner_tol=1e-2, inner_maxit=1000, maxit=1000, near=None, expand=0):
     """Solve A E = E_inc; returns (E, info) with the true residual added to info.
-    near = (radius, q): cube-integrated near-neighbour kernel entries (green.cube_kernel)."""
+    near = (radius, q): cube-integrated near-neighbour kernel entries (green.cube_kernel).
+    expand = e: expanded blocks (precond.find_blocks)."""
     A = FFTOperator(eps_r, h, k, near=near)
     Kinv = None
     if use_precond and np.any(block_id >= 0):
-        Kinv = BlockPreconditioner(eps_r, block_id, h, k, inner_tol, inner_maxit, near=near)
+        Kinv = BlockPreconditioner(eps_r, block_id, h, k, inner_tol, inner_maxit, near=near, expand=expand)
     E, info = bicgstab(A.apply, einc, tol, maxit, apply_Kinv=Kinv)
     info["true_rel_res"] = np.linalg.norm(einc - A.apply(E)) / np.linalg.norm(einc)
     return E, info

@@ -286,6 +286,8 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
     if (!(d->h > 0.0) || !std::isfinite(d->h)) return fail(VIE_EINVAL, "vie_grid_create: h must be positive");
     if (!d->eps_r) return fail(VIE_EINVAL, "vie_grid_create: eps_r is null");
     if (d->flags > VIE_GRID_INNER_PERSISTENT) return fail(VIE_EINVAL, "vie_grid_create: unknown flags");
+    if (d->block_expand < 0 || d->block_expand > 64)
+        return fail(VIE_EINVAL, "vie_grid_create: block_expand must be in [0, 64]");
 
     vie_grid* g = new vie_grid();
     auto bail = [&](int rc) { release_grid(g); return rc; };
@@ -351,13 +353,76 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
                     hi[3 * b + a] = std::max(hi[3 * b + a], c[a]);
                 }
             }
-    // group blocks by padded FFT shape of their bounding boxes
-    std::map<std::tuple<int, int, int>, std::vector<int>> bykey;
+    // the set each block is solved on: S_k itself, or with block_expand = E > 0 also every voxel with
+    // chi != 0 within Chebyshev distance E of S_k (restricted additive Schwarz: only S_k is kept).
+    // smask[b] covers the bounding box (slo, sext) of that set: 1 = S_k, 2 = halo, 0 = outside.
+    const int E = d->block_expand;
+    const int gn[3] = {g->nx, g->ny, g->nz};
+    std::vector<std::vector<uint8_t>> smask(K);
+    std::vector<int> slo(3 * K), sext(3 * K);
     for (int b = 0; b < K; ++b) {
-        int ext[3];
-        for (int a = 0; a < 3; ++a) ext[a] = hi[3 * b + a] - lo[3 * b + a] + 1;
-        bykey[std::make_tuple(padded_len(ext[2]), padded_len(ext[1]), padded_len(ext[0]))].push_back(b);
+        int elo[3], eext[3];
+        for (int a = 0; a < 3; ++a) {
+            elo[a] = std::max(0, lo[3 * b + a] - E);
+            eext[a] = std::min(gn[a] - 1, hi[3 * b + a] + E) - elo[a] + 1;
+        }
+        const int64_t ev = (int64_t)eext[0] * eext[1] * eext[2];
+        std::vector<uint8_t> own(ev, 0), dil;
+        auto at = [&](int x, int y, int z) { return ((int64_t)z * eext[1] + y) * eext[0] + x; };
+        for (int z = 0; z < eext[2]; ++z)
+            for (int y = 0; y < eext[1]; ++y)
+                for (int x = 0; x < eext[0]; ++x)
+                    own[at(x, y, z)] = bid[((int64_t)(z + elo[2]) * g->ny + y + elo[1]) * g->nx + x + elo[0]] == b;
+        dil = own;
+        for (int a = 0; a < 3 && E > 0; ++a) {          // separable dilation by a (2E+1)^3 cube
+            std::vector<uint8_t> nx_ = dil;
+            for (int z = 0; z < eext[2]; ++z)
+                for (int y = 0; y < eext[1]; ++y)
+                    for (int x = 0; x < eext[0]; ++x) {
+                        int c[3] = {x, y, z};
+                        uint8_t m = 0;
+                        for (int dd = -E; dd <= E && !m; ++dd) {
+                            int q[3] = {c[0], c[1], c[2]};
+                            q[a] += dd;
+                            if (q[a] >= 0 && q[a] < eext[a]) m = dil[at(q[0], q[1], q[2])];
+                        }
+                        nx_[at(x, y, z)] = m;
+                    }
+            dil.swap(nx_);
+        }
+        int blo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, bhi[3] = {-1, -1, -1};
+        std::vector<uint8_t> m(ev, 0);
+        for (int z = 0; z < eext[2]; ++z)
+            for (int y = 0; y < eext[1]; ++y)
+                for (int x = 0; x < eext[0]; ++x) {
+                    const int64_t gv = ((int64_t)(z + elo[2]) * g->ny + y + elo[1]) * g->nx + x + elo[0];
+                    const bool nonair = chi[gv].x != 0.0 || chi[gv].y != 0.0;
+                    const uint8_t v = own[at(x, y, z)] ? 1 : ((dil[at(x, y, z)] && nonair) ? 2 : 0);
+                    m[at(x, y, z)] = v;
+                    if (v) {
+                        int c[3] = {x, y, z};
+                        for (int a = 0; a < 3; ++a) {
+                            blo[a] = std::min(blo[a], c[a]);
+                            bhi[a] = std::max(bhi[a], c[a]);
+                        }
+                    }
+                }
+        for (int a = 0; a < 3; ++a) {
+            slo[3 * b + a] = elo[a] + blo[a];
+            sext[3 * b + a] = bhi[a] - blo[a] + 1;
+        }
+        std::vector<uint8_t>& sm = smask[b];
+        sm.assign((int64_t)sext[3 * b] * sext[3 * b + 1] * sext[3 * b + 2], 0);
+        for (int z = 0; z < sext[3 * b + 2]; ++z)
+            for (int y = 0; y < sext[3 * b + 1]; ++y)
+                for (int x = 0; x < sext[3 * b]; ++x)
+                    sm[((int64_t)z * sext[3 * b + 1] + y) * sext[3 * b] + x] = m[at(x + blo[0], y + blo[1], z + blo[2])];
     }
+    // group blocks by padded FFT shape of the bounding boxes of their sets
+    std::map<std::tuple<int, int, int>, std::vector<int>> bykey;
+    for (int b = 0; b < K; ++b)
+        bykey[std::make_tuple(padded_len(sext[3 * b + 2]), padded_len(sext[3 * b + 1]), padded_len(sext[3 * b]))]
+            .push_back(b);
     std::vector<int32_t> h_group(K), h_index(K), h_origin(3 * K);
     g->groups.resize(bykey.size());
     int gi = 0;
@@ -366,9 +431,9 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
         const std::vector<int>& mem = kv.second;
         int mx = 1, my = 1, mz = 1;
         for (int b : mem) {
-            mx = std::max(mx, hi[3 * b] - lo[3 * b] + 1);
-            my = std::max(my, hi[3 * b + 1] - lo[3 * b + 1] + 1);
-            mz = std::max(mz, hi[3 * b + 2] - lo[3 * b + 2] + 1);
+            mx = std::max(mx, sext[3 * b]);
+            my = std::max(my, sext[3 * b + 1]);
+            mz = std::max(mz, sext[3 * b + 2]);
         }
         gr.bs.nb = (int)mem.size();
         set_shape(gr.bs, mx, my, mz);
@@ -381,16 +446,17 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
             int b = mem[j];
             h_group[b] = gi;
             h_index[b] = j;
-            for (int a = 0; a < 3; ++a) gorig[3 * j + a] = h_origin[3 * b + a] = lo[3 * b + a];
-            for (int lz = 0; lz < mz; ++lz)
-                for (int ly = 0; ly < my; ++ly)
-                    for (int lx = 0; lx < mx; ++lx) {
-                        int x = lo[3 * b] + lx, y = lo[3 * b + 1] + ly, z = lo[3 * b + 2] + lz;
-                        if (x >= g->nx || y >= g->ny || z >= g->nz) continue;
+            for (int a = 0; a < 3; ++a) gorig[3 * j + a] = h_origin[3 * b + a] = slo[3 * b + a];
+            const int ex = sext[3 * b], ey = sext[3 * b + 1], ez = sext[3 * b + 2];
+            for (int lz = 0; lz < ez; ++lz)
+                for (int ly = 0; ly < ey; ++ly)
+                    for (int lx = 0; lx < ex; ++lx) {
+                        const uint8_t v = smask[b][((int64_t)lz * ey + ly) * ex + lx];
+                        if (!v) continue;
+                        int x = slo[3 * b] + lx, y = slo[3 * b + 1] + ly, z = slo[3 * b + 2] + lz;
                         int64_t gv = ((int64_t)z * g->ny + y) * g->nx + x;
-                        if (bid[gv] != b) continue;
                         int64_t l = (int64_t)j * box + ((int64_t)lz * my + ly) * mx + lx;
-                        gmask[l] = 1;
+                        gmask[l] = v;
                         gchi[l] = chi[gv];
                     }
         }
@@ -503,7 +569,22 @@ namespace vie {
 static std::vector<int> shape_signature(const vie_grid* g);
 }
 
+static int green_spectrum(vie_grid* g, double k0, int mask, const NearRule& near, cudaStream_t stream,
+                          vie_spectrum** out);
+
 extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t stream, vie_spectrum** out) {
+    return green_spectrum(g, k0, mask, NearRule(), (cudaStream_t)stream, out);
+}
+
+extern "C" int vie_green_spectrum_near(vie_grid* g, double k0, int mask, int32_t near_radius, int32_t near_order,
+                                       vie_stream_t stream, vie_spectrum** out) {
+    NearRule near;
+    VIE_TRY(near_rule(near_radius, near_order, &near));
+    return green_spectrum(g, k0, mask, near, (cudaStream_t)stream, out);
+}
+
+static int green_spectrum(vie_grid* g, double k0, int mask, const NearRule& near, cudaStream_t stream,
+                          vie_spectrum** out) {
     if (!g || !out) return fail(VIE_EINVAL, "vie_green_spectrum: null argument");
     *out = nullptr;
     if (!(k0 > 0.0) || !std::isfinite(k0)) return fail(VIE_EINVAL, "vie_green_spectrum: k0 must be positive");
@@ -541,7 +622,7 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
         sp->g128.push_back(G);
         sp->g64.push_back(G64);
         sp->go64.push_back(nullptr);
-        int rc = spectrum_build(g->full, k0, g->h, G, G64, nullptr, s);
+        int rc = spectrum_build(g->full, k0, g->h, G, G64, nullptr, s, &near);
         if (rc) return bail(rc);
     }
     sets.erase(sets.begin());
@@ -551,7 +632,7 @@ extern "C" int vie_green_spectrum(vie_grid* g, double k0, int mask, vie_stream_t
         int arc = dmalloc((void**)&G, n * sizeof(double2), "vie_green_spectrum");
         if (arc) return bail(arc);
         sp->g128.push_back(G);
-        int rc = green_sample(*bs, k0, g->h, G, s);
+        int rc = green_sample(*bs, k0, g->h, G, s, &near);
         if (!rc) rc = spectrum_fft<double2>(*bs, G, s);
         if (rc) return bail(rc);
         float2* G64 = nullptr;

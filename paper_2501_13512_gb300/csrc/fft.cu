@@ -847,11 +847,11 @@ __global__ void k_octant_compress(const double2* full, C* oct, int lx, int ly, i
 }
 
 int spectrum_build(const BoxSet& bs, double k0, double h, double2* oct128, float2* oct64, float2* full64,
-                   cudaStream_t s) {
+                   cudaStream_t s, const NearRule* near) {
     const int64_t n = 6 * bs.spec_elems();
     double2* G = nullptr;
     VIE_CK(cudaMallocAsync((void**)&G, n * sizeof(double2), s));
-    int rc = green_sample(bs, k0, h, G, s);
+    int rc = green_sample(bs, k0, h, G, s, near);
     if (!rc) rc = spectrum_fft<double2>(bs, G, s);
     const int64_t no = 6 * bs.oct_elems();
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((no + 255) / 256, 152 * 16));

@@ -3,6 +3,8 @@
 // block-diagonal preconditioner (Eq. 10).
 #include <math.h>
 
+#include <cmath>
+
 #include "vie_internal.cuh"
 
 namespace vie {
@@ -21,13 +23,40 @@ __device__ __forceinline__ bool wrap_offset(int m, int M, int b, int& d) {
     return false;
 }
 
+// The six components of k0^2 G(r) h^3 `scale` at a point r != 0 (Eq. 1:
+// k^2 G = g [(k^2 - jk/R - 1/R^2) I + (-k^2 + 3jk/R + 3/R^2) rhat rhat]), added to K.
+__device__ __forceinline__ void add_k2G(double rx, double ry, double rz, double k0, double hs, double wgt,
+                                        double2 (&K)[6]) {
+    const double inv4pi = 0.25 / 3.14159265358979323846;
+    const double R2 = rx * rx + ry * ry + rz * rz;
+    const double R = sqrt(R2);
+    double sn, cs;
+    sincos(k0 * R, &sn, &cs);
+    // g h^3 scale = e^{-jkR} / (4 pi R) h^3 scale
+    const double gm = inv4pi / R * hs * wgt;
+    const double2 g = make_double2(cs * gm, -sn * gm);
+    const double2 a = make_double2(k0 * k0 - 1.0 / R2, -k0 / R);
+    const double2 b = make_double2(-k0 * k0 + 3.0 / R2, 3.0 * k0 / R);
+    const double2 ga = cmul(g, a), gb = cmul(g, b);
+    const double u[3] = {rx / R, ry / R, rz / R};
+    const int P[6] = {0, 0, 0, 1, 1, 2}, Q[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const double uu = u[P[c]] * u[Q[c]];
+        double2 v = make_double2(gb.x * uu, gb.y * uu);
+        if (P[c] == Q[c]) v = v + ga;
+        K[c] = K[c] + v;
+    }
+}
+
 // K(D) = k0^2 G(D h) h^3 for D != 0 and s_self I at D = 0, times `scale`
-// (1 / (Mx My Mz), the inverse-FFT normalisation folded into the spectrum).
+// (1 / (Mx My Mz), the inverse-FFT normalisation folded into the spectrum);
+// offsets with 0 < max|D| <= near.radius take the mean of k0^2 G over the cube
+// of side h around D h instead (tensor Gauss-Legendre rule of order near.q).
 // Output: natural order [6][Mz][My][Mx], components xx, xy, xz, yy, yz, zz.
 __global__ void k_green_sample(double2* G, int Mx, int My, int Mz, int bx, int by, int bz,
-                               double k0, double h, double scale, double2 self) {
+                               double k0, double h, double scale, double2 self, NearRule near) {
     const int64_t vol = (int64_t)Mx * My * Mz;
-    const double inv4pi = 0.25 / 3.14159265358979323846;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < vol;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int ix = (int)(idx % Mx);
@@ -44,24 +73,18 @@ __global__ void k_green_sample(double2* G, int Mx, int My, int Mz, int bx, int b
                 K[3] = sd;
                 K[5] = sd;
             } else {
-                double rx = dx * h, ry = dy * h, rz = dz * h;
-                double R2 = rx * rx + ry * ry + rz * rz;
-                double R = sqrt(R2);
-                double sn, cs;
-                sincos(k0 * R, &sn, &cs);
-                // g h^3 scale = e^{-jkR} / (4 pi R) h^3 scale
-                double gm = inv4pi / R * h * h * h * scale;
-                double2 g = make_double2(cs * gm, -sn * gm);
-                double2 a = make_double2(k0 * k0 - 1.0 / R2, -k0 / R);
-                double2 b = make_double2(-k0 * k0 + 3.0 / R2, 3.0 * k0 / R);
-                double2 ga = cmul(g, a), gb = cmul(g, b);
-                double u[3] = {rx / R, ry / R, rz / R};
-                const int P[6] = {0, 0, 0, 1, 1, 2}, Q[6] = {0, 1, 2, 1, 2, 2};
-                for (int c = 0; c < 6; ++c) {
-                    double uu = u[P[c]] * u[Q[c]];
-                    double2 v = make_double2(gb.x * uu, gb.y * uu);
-                    if (P[c] == Q[c]) v = v + ga;
-                    K[c] = v;
+                const double hs = h * h * h * scale;
+                const int dmax = max(abs(dx), max(abs(dy), abs(dz)));
+                if (dmax <= near.radius) {
+                    // mean over the cube: weights w_i w_j w_l / 8 of the rule on [-1, 1]^3
+                    for (int l = 0; l < near.q; ++l)
+                        for (int j = 0; j < near.q; ++j)
+                            for (int i = 0; i < near.q; ++i)
+                                add_k2G((dx + 0.5 * near.t[i]) * h, (dy + 0.5 * near.t[j]) * h,
+                                        (dz + 0.5 * near.t[l]) * h, k0, hs,
+                                        0.125 * near.w[i] * near.w[j] * near.w[l], K);
+                } else {
+                    add_k2G(dx * h, dy * h, dz * h, k0, hs, 1.0, K);
                 }
             }
         }
@@ -69,7 +92,52 @@ __global__ void k_green_sample(double2* G, int Mx, int My, int Mz, int bx, int b
     }
 }
 
-int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t s) {
+// Gauss-Legendre rule of order q on [-1, 1]: the nodes are the roots of the Legendre polynomial
+// P_q, found by Newton's method from the Chebyshev-like first guesses cos(pi (i + 3/4) / (q + 1/2)),
+// with P_q and P_q' from the three-term recurrence; weights 2 / ((1 - t^2) P_q'(t)^2).
+int near_rule(int radius, int q, NearRule* out) {
+    NearRule r;
+    if (radius < 0 || radius > 8) return fail(VIE_EINVAL, "near-field radius must be in [0, 8]");
+    r.radius = radius;
+    if (radius == 0) {
+        *out = r;
+        return VIE_OK;
+    }
+    if (q < 1 || q > kNearMaxOrder) return fail(VIE_EINVAL, "near-field quadrature order must be in [1, 16]");
+    r.q = q;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < q; ++i) {
+        double t = std::cos(pi * (i + 0.75) / (q + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;                 // P_0, P_1
+            for (int n = 2; n <= q; ++n) {
+                const double p2 = ((2.0 * n - 1.0) * t * p1 - (n - 1.0) * p0) / n;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pq = q == 1 ? t : p1, pm = q == 1 ? 1.0 : p0;   // P_q, P_{q-1}
+            dp = q * (t * pq - pm) / (t * t - 1.0);                      // P_q'
+            const double dt = pq / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        // recompute the derivative at the converged node
+        double p0 = 1.0, p1 = t;
+        for (int n = 2; n <= q; ++n) {
+            const double p2 = ((2.0 * n - 1.0) * t * p1 - (n - 1.0) * p0) / n;
+            p0 = p1;
+            p1 = p2;
+        }
+        const double pq = q == 1 ? t : p1, pm = q == 1 ? 1.0 : p0;
+        dp = q * (t * pq - pm) / (t * t - 1.0);
+        r.t[i] = t;
+        r.w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+    *out = r;
+    return VIE_OK;
+}
+
+int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t s, const NearRule* near) {
     // equivalent-sphere self term: (2/3)[(1 + jka) e^{-jka} - 1] - 1/3
     const double a = h * cbrt(3.0 / (4.0 * 3.14159265358979323846));
     const double ka = k0 * a;
@@ -78,8 +146,9 @@ int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t
     double2 self = make_double2((2.0 / 3.0) * (c + ka * sn - 1.0) - 1.0 / 3.0, (2.0 / 3.0) * (ka * c - sn));
     const double scale = 1.0 / ((double)bs.Mx * bs.My * bs.Mz);
     prof_begin(s, PK_SPECTRUM, VIE_C128, 0, 6 * bs.spec_elems() * 16, false);
+    const NearRule rule = near ? *near : NearRule();
     k_green_sample<<<grid_1d(bs.spec_elems()), 256, 0, s>>>(G, bs.Mx, bs.My, bs.Mz, bs.bx, bs.by, bs.bz,
-                                                            k0, h, scale, self);
+                                                            k0, h, scale, self, rule);
     prof_end(s);
     VIE_CK(cudaGetLastError());
     return VIE_OK;
@@ -155,7 +224,8 @@ __global__ void k_gather(const C* src, C* out, const uint8_t* mask, const int32_
     }
 }
 
-// y = x_k on the voxels of block k (the blocks are disjoint, so no write conflicts).
+// y = x_k on the voxels of block k (mask 1; the blocks are disjoint, so no write conflicts). Halo
+// voxels of an expanded block (mask 2) belong to another block or to none and are not written.
 template <class C>
 __global__ void k_scatter(const C* xk, C* y, const uint8_t* mask, const int32_t* origin,
                           int nb, int bx, int by, int bz, int nx, int ny, int nz) {
@@ -167,7 +237,7 @@ __global__ void k_scatter(const C* xk, C* y, const uint8_t* mask, const int32_t*
         int64_t l = idx % box;
         int64_t bc = idx / box;
         int c = (int)(bc % 3), b = (int)(bc / 3);
-        if (!mask[(int64_t)b * box + l]) continue;
+        if (mask[(int64_t)b * box + l] != 1) continue;
         int lx = (int)(l % bx), ly = (int)((l / bx) % by), lz = (int)(l / ((int64_t)bx * by));
         int gx = origin[3 * b] + lx, gy = origin[3 * b + 1] + ly, gz = origin[3 * b + 2] + lz;
         y[c * N + ((int64_t)gz * ny + gy) * nx + gx] = xk[idx];

@@ -268,11 +268,21 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* tw = nu
 // Green spectrum of one box shape at wavenumber k0 (FP64 samples and FFT in a
 // stream-ordered temporary), written to any of: oct128 / oct64 (octant
 // layout [6][Mz/2+1][My/2+1][Mx/2+1]), full64 (full layout [6][Mz][My][Mx]).
+// Cube-integrated near-neighbour entries (an accuracy variant; the paper does not say how
+// near couplings are integrated): K(D) = mean over the cube of side h centred at D h of
+// k0^2 G, times h^3, for 0 < max|D| <= radius, by tensor Gauss-Legendre quadrature of order q.
+constexpr int kNearMaxOrder = 16;
+struct NearRule {
+    int radius = 0;                       // 0: point sampling everywhere
+    int q = 0;
+    double t[kNearMaxOrder], w[kNearMaxOrder];   // nodes and weights on [-1, 1]
+};
+int near_rule(int radius, int q, NearRule* out);   // VIE_EINVAL outside radius [0, 8], q [1, 16]
 int spectrum_build(const BoxSet& bs, double k0, double h, double2* oct128, float2* oct64, float2* full64,
-                   cudaStream_t s);
+                   cudaStream_t s, const NearRule* near = nullptr);
 
 // ---------------------------------------------------------------- green.cu
-int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t s);
+int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t s, const NearRule* near = nullptr);
 int convert_c128_to_c64(const double2* a, float2* b, int64_t n, cudaStream_t s);
 int plane_wave_launch(const vie_grid* g, double k0, const double* khat, const double* pol,
                       int precision, void* out, cudaStream_t s);

@@ -34,7 +34,8 @@ class VieError(RuntimeError):
 
 class GridDesc(ctypes.Structure):
     _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("h", c_double),
-                ("eps_r", POINTER(c_double)), ("block_id", POINTER(c_int32)), ("flags", c_uint32)]
+                ("eps_r", POINTER(c_double)), ("block_id", POINTER(c_int32)), ("flags", c_uint32),
+                ("block_expand", c_int32)]
 
 
 class GridInfo(ctypes.Structure):
@@ -99,6 +100,7 @@ def load(path=LIB_PATH):
         "vie_grid_destroy": ([P], c_int),
         "vie_grid_get_info": ([P, POINTER(GridInfo)], c_int),
         "vie_green_spectrum": ([P, c_double, c_int, P, POINTER(P)], c_int),
+        "vie_green_spectrum_near": ([P, c_double, c_int, c_int32, c_int32, P, POINTER(P)], c_int),
         "vie_spectrum_release": ([P], c_int),
         "vie_plane_wave": ([P, c_double, POINTER(c_double), POINTER(c_double), c_int, P, P], c_int),
         "vie_matvec": ([P, P, c_int, P, P, P], c_int),
@@ -208,7 +210,7 @@ class Spectrum:
 class Grid:
     """A voxel grid with its contrast and block partition (vie_grid)."""
 
-    def __init__(self, eps_r, h, block_id=None, inner=INNER_AUTO):
+    def __init__(self, eps_r, h, block_id=None, inner=INNER_AUTO, expand=0):
         lib = load()
         eps_r = np.ascontiguousarray(eps_r, dtype=np.complex128)
         nz, ny, nx = eps_r.shape
@@ -218,14 +220,15 @@ class Grid:
         self._eps = eps_r.view(np.float64).reshape(-1)
         self._bid = None if block_id is None else np.ascontiguousarray(block_id, dtype=np.int32).reshape(-1)
         d = GridDesc(nx, ny, nz, self.h, self._eps.ctypes.data_as(POINTER(c_double)),
-                     None if self._bid is None else self._bid.ctypes.data_as(POINTER(c_int32)), int(inner))
+                     None if self._bid is None else self._bid.ctypes.data_as(POINTER(c_int32)), int(inner),
+                     int(expand))
         handle = c_void_p()
         _check(lib.vie_grid_create(byref(d), byref(handle)))
         self.handle = handle
 
     @classmethod
-    def from_workload(cls, w, inner=INNER_AUTO):
-        return cls(w.eps_r, w.h, w.block_id if w.use_precond else None, inner)
+    def from_workload(cls, w, inner=INNER_AUTO, expand=0):
+        return cls(w.eps_r, w.h, w.block_id if w.use_precond else None, inner, expand)
 
     def info(self):
         inf = GridInfo()
@@ -257,9 +260,14 @@ class Grid:
         import torch
         return torch.empty((3,) + self.shape, dtype=_dtype(precision), device="cuda")
 
-    def spectrum(self, k0, precision=C128 | C64):
+    def spectrum(self, k0, precision=C128 | C64, near=None):
+        """near = (radius, order): cube-integrated near-neighbour entries (vie_green_spectrum_near)."""
         h = c_void_p()
-        _check(load().vie_green_spectrum(self.handle, float(k0), int(precision), _stream(), byref(h)))
+        if near is None:
+            _check(load().vie_green_spectrum(self.handle, float(k0), int(precision), _stream(), byref(h)))
+        else:
+            _check(load().vie_green_spectrum_near(self.handle, float(k0), int(precision), int(near[0]), int(near[1]),
+                                                  _stream(), byref(h)))
         return Spectrum(self, h, float(k0), precision)
 
     def plane_wave(self, k0, khat, pol, precision=C128, out=None):

@@ -74,6 +74,10 @@ def test_argument_validation_without_gpu():
         assert vie.last_error()
     d = vie.GridDesc(2, 2, 1, 1.0, eps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, 7)
     assert lib.vie_grid_create(ctypes.byref(d), ctypes.byref(ctypes.c_void_p())) == vie.VIE_EINVAL
+    for expand in (-1, 65):
+        d = vie.GridDesc(2, 2, 1, 1.0, eps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, 0, expand)
+        assert lib.vie_grid_create(ctypes.byref(d), ctypes.byref(ctypes.c_void_p())) == vie.VIE_EINVAL
+        assert "block_expand" in vie.last_error()
     for count in (0, 21846):
         b = vie.BatchDesc(2, 2, 1, 1.0, count, eps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
         assert lib.vie_batch_create(ctypes.byref(b), ctypes.byref(ctypes.c_void_p())) == vie.VIE_EINVAL

@@ -131,3 +131,60 @@ def test_optical_theorem_soft():
     c_abs = k * np.sum(-np.imag(w.eps_r) * np.sum(np.abs(E) ** 2, 0)) * w.h ** 3
     assert c_ext > 0
     assert abs(c_ext - (c_sca + c_abs)) <= 0.1 * c_ext
+
+
+# ---------------------------------------------------------------- expanded blocks
+def _dense_expanded(eps_r, bid, b, expand):
+    """Restricted additive Schwarz by dense LU: each block solved on S_k+, its own voxels kept."""
+    A = mvm.dense_operator(eps_r, H, K0)
+    N = eps_r.size
+    chi_nz = ((eps_r - 1.0) != 0).ravel()
+    y = b.ravel().copy()
+    for blk in precond.find_blocks(bid, expand, (eps_r - 1.0) != 0):
+        sel = np.zeros(bid.shape, bool)
+        sel[blk.slices] = blk.mask
+        core = np.zeros(bid.shape, bool)
+        core[blk.slices] = blk.core
+        idx = np.nonzero(np.tile(sel.ravel(), 3))[0]
+        xk = np.linalg.solve(A[np.ix_(idx, idx)], b.ravel()[idx])
+        keep = np.tile(core.ravel(), 3)[idx]
+        y[idx[keep]] = xk[keep]
+        assert np.all(chi_nz[sel.ravel()] | core.ravel()[sel.ravel()])   # halo voxels are never air
+    return y.reshape(b.shape)
+
+
+@pytest.mark.parametrize("expand", [1, 2])
+def test_expanded_blocks_match_dense_lu(expand):
+    eps_r, bid, b = inputs.random_case((6, 5, 4), seed=33, block_grid=(3, 3, 2))
+    P = precond.BlockPreconditioner(eps_r, bid, H, K0, inner_tol=1e-13, inner_maxit=500, expand=expand)
+    yref = _dense_expanded(eps_r, bid, b, expand)
+    assert np.linalg.norm(P(b) - yref) <= 1e-10 * np.linalg.norm(yref)
+    # the expanded sets really grow, and the plain blocks are the expand = 0 case
+    plain = precond.find_blocks(bid)
+    grown = precond.find_blocks(bid, expand, (eps_r - 1.0) != 0)
+    assert sum(g.mask.sum() for g in grown) > sum(p.mask.sum() for p in plain)
+    assert all(np.array_equal(p.mask, p.core) for p in plain)
+    assert all(g.core.sum() == p.mask.sum() for g, p in zip(grown, plain))
+
+
+def test_expanded_blocks_reaching_every_voxel_are_exact_on_the_blocks():
+    # every non-air voxel lies in some block; with an expansion that covers the grid each block solves
+    # the closed system of all non-air voxels, so y equals A^-1 b on the blocks' voxels
+    eps_r, bid, b = inputs.random_case((5, 4, 4), seed=34, block_grid=(3, 2, 2))
+    A = mvm.dense_operator(eps_r, H, K0)
+    x = np.linalg.solve(A, b.ravel()).reshape(b.shape)
+    P = precond.BlockPreconditioner(eps_r, bid, H, K0, inner_tol=1e-13, inner_maxit=800, expand=5)
+    y = P(b)
+    on = bid >= 0
+    assert np.linalg.norm(y[:, on] - x[:, on]) <= 1e-10 * np.linalg.norm(x[:, on])
+    assert np.array_equal(y[:, ~on], b[:, ~on])
+
+
+def test_expanded_blocks_same_solution_fewer_outer_iterations():
+    # the preconditioner changes the iterations, not the solution of A E = E_inc
+    w = inputs.metasurface(cells=2, period=8, nz=6, seed=5, block_cells=1)
+    ein = solve.plane_wave(w.n, w.h, w.k0, w.khat, w.pol)
+    e0, i0 = solve.solve(w.eps_r, w.block_id, w.h, w.k0, ein, tol=1e-10, inner_tol=1e-2)
+    e2, i2 = solve.solve(w.eps_r, w.block_id, w.h, w.k0, ein, tol=1e-10, inner_tol=1e-2, expand=2)
+    assert np.linalg.norm(e2 - e0) <= 1e-8 * np.linalg.norm(e0)
+    assert i2["iters"] <= i0["iters"]
