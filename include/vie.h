@@ -279,6 +279,51 @@ int vie_batch_solve(vie_batch* batch, const double* k0s, const void* einc_dev,
                     void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
                     vie_solve_stats* stats);
 
+/* ---- The paper's rooftop / pulse discretisation (Section II.A, Eqs. 5-9). ----
+ * Unknown w = J / (j w eps0) (units of E; w = chi E in the continuum), expanded in rooftops (Eq. 5):
+ * component a lives on the face between cell c and cell c + e_a, stored at index c of a vector
+ * [3][nz][ny][nx]; a face carries a rooftop when both of its cells are inside the grid and non-air
+ * (the normal current vanishes on the object's surface; other entries are 0). Tested with pulses on
+ * the dual cells (Eq. 6) the equation reads
+ *   (1/chi) Gram w - k0^2 int g w - grad int g div w = E_inc,
+ * the contrast and vector-potential parts of L^c (Eq. 8) and the scalar potential of L^q (Eq. 9,
+ * read as acting on w_j), with the sign of Eq. 4: the Gram of rooftops and pulses gives 3/8 per half
+ * cell (times 1/chi of that cell) on the face and 1/8 to its two neighbours along a; cell charges are
+ * the divergence of the rooftops; potentials use the integral of g over each cell (h^3 g at the cell
+ * centre, the equivalent sphere at the source cell). The operator is Toeplitz in the face indices
+ * and runs through the same FFT passes as vie_matvec, with nine spectra. */
+typedef struct vie_rooftop vie_rooftop;
+
+/* Builds the rooftop operator of the grid's permittivity at wavenumber k0 (spectra in FP64, also
+ * rounded to complex64 with VIE_C64 in precision_mask), with its workspace. The operator uses the
+ * grid's FFT scratch: calls on it and on the grid must be ordered on one stream. Release it before
+ * the grid. Errors: VIE_EINVAL, VIE_EBUSY, VIE_ENOMEM, VIE_ECUDA. */
+int vie_rooftop_create(vie_grid* grid, double k0, int precision_mask, vie_stream_t stream, vie_rooftop** out);
+
+/* Waits for the device, then frees the operator. */
+int vie_rooftop_release(vie_rooftop* op);
+
+/* E_inc = pol exp(-j k0 khat . r) at the face centres of every component (0 on faces without a
+ * rooftop), into a vector of `precision`. Asynchronous. */
+int vie_rooftop_incident(const vie_rooftop* op, const double* khat, const double* pol, int precision,
+                         void* out_dev, vie_stream_t stream);
+
+/* y = A w, DEVICE vectors of `precision` ([3][nz][ny][nx]), not overlapping; entries of faces without
+ * a rooftop are ignored in w and 0 in y. Asynchronous. Errors: VIE_EINVAL. */
+int vie_rooftop_matvec(vie_rooftop* op, int precision, const void* w_dev, void* y_dev, vie_stream_t stream);
+
+/* Solves A w = b (complex128, DEVICE, distinct) by unpreconditioned BiCGSTAB from w = 0 to
+ * ||b - A w|| <= tol ||b|| (recursive residual, reported in stats->true_rel_res) or maxit
+ * iterations; stats may be NULL (outer_iters, matvecs_c128, status, elapsed_ms are set). Returns
+ * VIE_OK, VIE_ENOTCONV, VIE_EBREAKDOWN, VIE_ETIMEOUT (bounded host waits, 0 = 60000 ms), VIE_EINVAL. */
+int vie_rooftop_solve(vie_rooftop* op, const void* b_dev, void* w_dev, double tol, int32_t maxit,
+                      double wait_timeout_ms, vie_stream_t stream, vie_solve_stats* stats);
+
+/* Bistatic RCS of a rooftop solution w (complex128, DEVICE): as vie_far_field_rcs with
+ * P(u) = sum over faces of w h^3 exp(j k0 u . r_face). HOST directions and results; synchronises. */
+int vie_rooftop_far_field_rcs(const vie_rooftop* op, const void* w_dev, int32_t ndir, const double* dirs_host,
+                              double* rcs_host, vie_stream_t stream);
+
 /* Bistatic radar cross section of a solved field (the far-zone limit of the
  * scattered field of Eq. 1 with J = j w eps0 chi E; Section III's RCS
  * comparisons, Figs. 1-2): for each direction u,

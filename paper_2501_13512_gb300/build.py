@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 SOURCES = ["fft.cu", "krylov.cu", "fields.cu", "api.cu", "profile.cu", "inner.cu", "noalloc.cu", "batch.cu",
-           "farfield.cu"]
+           "farfield.cu", "rooftop.cu"]
 HEADERS = [os.path.join(CSRC, "vie_internal.cuh"), os.path.join(CSRC, "fft_core.cuh"), os.path.join(CSRC, "fft_reg.cuh"),
            os.path.join(ROOT, "include", "vie.h")]
 LIB = os.path.join(HERE, "libvie.so")

@@ -83,6 +83,17 @@ using namespace vie;
 extern "C" int vie_far_field_rcs(const vie_grid* g, double k0, const void* e_dev, int32_t ndir, const double* dirs_host,
                                  double* rcs_host, vie_stream_t stream) {
     if (!g || !e_dev || !dirs_host || !rcs_host) return fail(VIE_EINVAL, "vie_far_field_rcs: null argument");
+    return far_field_rcs_impl(g->nx, g->ny, g->nz, g->h, k0, (const double2*)e_dev, g->full.chi128, nullptr, ndir,
+                              dirs_host, rcs_host, (cudaStream_t)stream);
+}
+
+namespace vie {
+
+// P(u) = sum_j w_j E_j h^3 exp(j k0 u . (r_j + shift_c e_c)) per component c (w = chi for the
+// collocation field; w = 1 and shift = h/2 for rooftop currents on faces), then the RCS.
+int far_field_rcs_impl(int nx, int ny, int nz, double h, double k0, const double2* e_dev, const double2* wts,
+                       const double* shift, int32_t ndir, const double* dirs_host, double* rcs_host, cudaStream_t s) {
+    if (!e_dev || !dirs_host || !rcs_host) return fail(VIE_EINVAL, "vie_far_field_rcs: null argument");
     if (ndir < 1 || ndir > (1 << 20)) return fail(VIE_EINVAL, "vie_far_field_rcs: ndir must be in [1, 2^20]");
     if (!(k0 > 0.0) || !std::isfinite(k0)) return fail(VIE_EINVAL, "vie_far_field_rcs: k0 must be positive");
     std::vector<double3> dirs(ndir);
@@ -92,8 +103,7 @@ extern "C" int vie_far_field_rcs(const vie_grid* g, double k0, const void* e_dev
         if (!(std::fabs(n2 - 1.0) <= 1e-9)) return fail(VIE_EINVAL, "vie_far_field_rcs: directions must be unit vectors");
         dirs[i] = make_double3(ux, uy, uz);
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    const int slabs = std::min(kFfSlabs, g->nz);
+    const int slabs = std::min(kFfSlabs, nz);
     double3* d_dirs = nullptr;
     double2* d_part = nullptr;
     const size_t part_n = (size_t)ndir * slabs * 3;
@@ -107,10 +117,9 @@ extern "C" int vie_far_field_rcs(const vie_grid* g, double k0, const void* e_dev
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
     }
     if (!rc) {
-        const size_t smem = (size_t)(g->nx + g->ny + g->nz + 3 * (kFfThreads / 32)) * sizeof(double2);
-        prof_begin(s, PK_FIELD, VIE_C128, 0, (int64_t)ndir * g->N * 64, false);
-        k_far_field<<<dim3(ndir, slabs), kFfThreads, smem, s>>>((const double2*)e_dev, g->full.chi128, d_dirs, g->nx,
-                                                                 g->ny, g->nz, g->h, k0, d_part);
+        const size_t smem = (size_t)(nx + ny + nz + 3 * (kFfThreads / 32)) * sizeof(double2);
+        prof_begin(s, PK_FIELD, VIE_C128, 0, (int64_t)ndir * nx * ny * nz * 64, false);
+        k_far_field<<<dim3(ndir, slabs), kFfThreads, smem, s>>>(e_dev, wts, d_dirs, nx, ny, nz, h, k0, d_part);
         prof_end(s);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "k_far_field launch", __FILE__, __LINE__);
@@ -123,7 +132,7 @@ extern "C" int vie_far_field_rcs(const vie_grid* g, double k0, const void* e_dev
     if (d_part) cudaFreeAsync(d_part, s);
     if (d_dirs) cudaFreeAsync(d_dirs, s);
     if (rc) return rc;
-    const double h3 = g->h * g->h * g->h;
+    const double h3 = h * h * h;
     const double pref = k0 * k0 * k0 * k0 / (4.0 * 3.141592653589793238462643383279502884);
     for (int i = 0; i < ndir; ++i) {
         double2 P[3];
@@ -133,6 +142,14 @@ extern "C" int vie_far_field_rcs(const vie_grid* g, double k0, const void* e_dev
             P[c] = make_double2(P[c].x * h3, P[c].y * h3);
         }
         const double3 u = dirs[i];
+        if (shift) {
+            const double uc[3] = {u.x, u.y, u.z};
+            for (int c = 0; c < 3; ++c) {
+                double sn, cs;
+                sincos(k0 * uc[c] * shift[c], &sn, &cs);
+                P[c] = cmul(P[c], make_double2(cs, sn));
+            }
+        }
         // (I - u u) P = P - u (u . P)
         const double2 up = make_double2(u.x * P[0].x + u.y * P[1].x + u.z * P[2].x,
                                         u.x * P[0].y + u.y * P[1].y + u.z * P[2].y);
@@ -146,3 +163,5 @@ extern "C" int vie_far_field_rcs(const vie_grid* g, double k0, const void* e_dev
     }
     return VIE_OK;
 }
+
+}  // namespace vie

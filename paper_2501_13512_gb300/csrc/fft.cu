@@ -159,6 +159,7 @@ template <class C> struct ZArgs {
     const C* tw;
     int ncols, nzb, lL, ltc, twshift;
     int oct, lx, ly;      // octant-compressed spectrum; log2 Mx, log2 My
+    int nine;             // nine full spectra G_ab (3a + b), general 3x3 multiply
     int64_t axis, comp_stride, box_stride, gcomp;
     int* units;
 };
@@ -199,6 +200,15 @@ __global__ void __launch_bounds__(kThreads) k_zgreen(ZArgs<C> a) {
             g += ((int64_t)qz * ((1 << a.ly) / 2 + 1) + qy) * ((1 << a.lx) / 2 + 1) + qx;
         } else {
             g += i * a.axis + col0 + c;
+        }
+        if (a.nine) {
+            C* p = buf + i * pitch + c;
+            const C X = p[0], Y = p[TC], Z = p[2 * TC];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                p[r * TC] = cmul(g[(3 * r) * a.gcomp], X) + cmul(g[(3 * r + 1) * a.gcomp], Y) +
+                            cmul(g[(3 * r + 2) * a.gcomp], Z);
+            continue;
         }
         C gxx = g[0], gxy = g[a.gcomp], gxz = g[2 * a.gcomp];
         C gyy = g[3 * a.gcomp], gyz = g[4 * a.gcomp], gzz = g[5 * a.gcomp];
@@ -724,7 +734,7 @@ template <> const float2* chi_ptr<float2>(const BoxSet& bs) { return bs.chi64; }
 
 template <class C>
 int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st, cudaStream_t s,
-              const Twiddles* twp, const C* const* Gb) {
+              const Twiddles* twp, const C* const* Gb, const C* xupd, bool nine) {
     Twiddles tw;
     if (twp) tw = *twp;
     else VIE_TRY(get_twiddles(&tw));
@@ -741,7 +751,7 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     const int64_t bv = 3LL * box * es;                            // x or y per box
     const Prof px{PK_X_FWD, bv + box * es + b1, 0};
     const Prof py{PK_Y_FWD, b1 + b2, 0};
-    const Prof pz{PK_Z_GREEN, 2 * b2, 6LL * (bs.oct ? bs.oct_elems() : bs.spec_elems()) * es};
+    const Prof pz{PK_Z_GREEN, 2 * b2, (nine ? 9LL : 6LL) * (bs.oct ? bs.oct_elems() : bs.spec_elems()) * es};
     const Prof piy{PK_Y_INV, b2 + b1, 0};
     const Prof pix{PK_X_INV, b1 + 2 * bv + (bs.mask ? box : 0), 0};
 
@@ -771,6 +781,8 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
     z.axis = planeXY; z.comp_stride = (int64_t)bs.bz * planeXY; z.box_stride = 3 * z.comp_stride;
     z.gcomp = bs.oct ? bs.oct_elems() : (int64_t)bs.Mz * planeXY;
     z.oct = bs.oct ? 1 : 0; z.lx = bs.lx; z.ly = bs.ly;
+    z.nine = nine ? 1 : 0;
+    if (nine && bs.oct) return fail(VIE_EINVAL, "mvm_boxes: nine spectra need the full layout");
     VIE_TRY(launch_zgreen<C>(z, bs.nb, pz, s));
 
     // pass Y inverse: keep y < by
@@ -782,14 +794,14 @@ int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st
 
     // pass X inverse: keep x < bx, y = x - u
     RowArgs<C> ix = rx;
-    ix.in = w1; ix.out = y; ix.xin = x; ix.mask = bs.mask; ix.chi = nullptr;
+    ix.in = w1; ix.out = y; ix.xin = xupd ? xupd : x; ix.mask = bs.mask; ix.chi = nullptr;
     ix.in_stride = bs.Mx; ix.out_stride = bs.bx; ix.n_in = bs.Mx; ix.n_out = bs.bx;
     VIE_TRY((launch_rows<C, ROW_INV_UPDATE>(ix, pix, s)));
     return VIE_OK;
 }
 
 template <class C>
-int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* twp) {
+int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* twp, int ncomp) {
     Twiddles tw;
     if (twp) tw = *twp;
     else VIE_TRY(get_twiddles(&tw));
@@ -800,7 +812,7 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* twp) {
 
     RowArgs<C> rx{};
     rx.in = G; rx.out = G; rx.tw = T;
-    rx.nrows = 6 * (int64_t)bs.Mz * bs.My;
+    rx.nrows = ncomp * (int64_t)bs.Mz * bs.My;
     rx.in_stride = bs.Mx; rx.out_stride = bs.Mx; rx.n_in = bs.Mx; rx.n_out = bs.Mx;
     rx.lL = bs.lx; rx.twshift = kLogLmax - bs.lx;
     rx.rows_per_box = (int)std::min<int64_t>(rx.nrows, 1 << 30); rx.plane = 1; rx.bx = bs.Mx;
@@ -812,7 +824,7 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* twp) {
     cy.in_axis = cy.out_axis = bs.Mx;
     cy.in_s1 = cy.out_s1 = planeXY;
     cy.in_s2 = cy.out_s2 = vol;
-    VIE_TRY((launch_cols<C, true>(cy, bs.Mz, 6, Prof{PK_SPECTRUM, 2 * vol * es, 0}, s)));
+    VIE_TRY((launch_cols<C, true>(cy, bs.Mz, ncomp, Prof{PK_SPECTRUM, 2 * vol * es, 0}, s)));
 
     ColArgs<C> cz{};
     cz.in = G; cz.out = G; cz.tw = T; cz.b2_per_box = 1;
@@ -820,7 +832,7 @@ int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* twp) {
     cz.in_axis = cz.out_axis = planeXY;
     cz.in_s1 = cz.out_s1 = 0;
     cz.in_s2 = cz.out_s2 = vol;
-    VIE_TRY((launch_cols<C, true>(cz, 1, 6, Prof{PK_SPECTRUM, 2 * vol * es, 0}, s)));
+    VIE_TRY((launch_cols<C, true>(cz, 1, ncomp, Prof{PK_SPECTRUM, 2 * vol * es, 0}, s)));
     return VIE_OK;
 }
 
@@ -874,9 +886,9 @@ int spectrum_build(const BoxSet& bs, double k0, double h, double2* oct128, float
 }
 
 template int mvm_boxes<double2>(const BoxSet&, const double2*, const double2*, double2*, const SegState*, cudaStream_t,
-                                const Twiddles*, const double2* const*);
+                                const Twiddles*, const double2* const*, const double2*, bool);
 template int mvm_boxes<float2>(const BoxSet&, const float2*, const float2*, float2*, const SegState*, cudaStream_t,
-                               const Twiddles*, const float2* const*);
-template int spectrum_fft<double2>(const BoxSet&, double2*, cudaStream_t, const Twiddles*);
+                               const Twiddles*, const float2* const*, const float2*, bool);
+template int spectrum_fft<double2>(const BoxSet&, double2*, cudaStream_t, const Twiddles*, int);
 
 }  // namespace vie

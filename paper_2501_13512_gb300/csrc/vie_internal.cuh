@@ -262,9 +262,13 @@ void prof_end(cudaStream_t s);
 // Gb: optional device array of one spectrum pointer per box (null: G for every box)
 template <class C>
 int mvm_boxes(const BoxSet& bs, const C* G, const C* x, C* y, const SegState* st,
-              cudaStream_t s, const Twiddles* tw = nullptr, const C* const* Gb = nullptr);
+              cudaStream_t s, const Twiddles* tw = nullptr, const C* const* Gb = nullptr,
+              const C* xupd = nullptr, bool nine = false);
+// xupd: the vector of the last pass's update y = xupd - u (default x); nine: G holds nine full
+// spectra G_ab (a, b = x, y, z; index 3a + b) and the z pass multiplies by the general 3x3 matrix.
 template <class C>
-int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* tw = nullptr);   // in place, 6 components
+int spectrum_fft(const BoxSet& bs, C* G, cudaStream_t s, const Twiddles* tw = nullptr,
+                 int ncomp = 6);   // in place, ncomp components
 // Green spectrum of one box shape at wavenumber k0 (FP64 samples and FFT in a
 // stream-ordered temporary), written to any of: oct128 / oct64 (octant
 // layout [6][Mz/2+1][My/2+1][Mx/2+1]), full64 (full layout [6][Mz][My][Mx]).
@@ -284,6 +288,10 @@ int spectrum_build(const BoxSet& bs, double k0, double h, double2* oct128, float
 // ---------------------------------------------------------------- green.cu
 int green_sample(const BoxSet& bs, double k0, double h, double2* G, cudaStream_t s, const NearRule* near = nullptr);
 int convert_c128_to_c64(const double2* a, float2* b, int64_t n, cudaStream_t s);
+// Bistatic RCS of sum_j wts_j E_j h^3 exp(j k0 u . r_j) over voxel centres r_j, component c shifted by
+// shift[c] along its own axis (shift may be null). Synchronises s.
+int far_field_rcs_impl(int nx, int ny, int nz, double h, double k0, const double2* e_dev, const double2* wts,
+                       const double* shift, int32_t ndir, const double* dirs_host, double* rcs_host, cudaStream_t s);
 int plane_wave_launch(const vie_grid* g, double k0, const double* khat, const double* pol,
                       int precision, void* out, cudaStream_t s);
 

@@ -114,6 +114,12 @@ def load(path=LIB_PATH):
         "vie_batch_get_info": ([P, POINTER(c_int64), POINTER(c_int32)], c_int),
         "vie_profile_enable": ([c_int], c_int),
         "vie_profile_read": ([POINTER(KernelStat), c_int, POINTER(c_int), POINTER(c_int64)], c_int),
+        "vie_rooftop_create": ([P, c_double, c_int, P, POINTER(P)], c_int),
+        "vie_rooftop_release": ([P], c_int),
+        "vie_rooftop_incident": ([P, POINTER(c_double), POINTER(c_double), c_int, P, P], c_int),
+        "vie_rooftop_matvec": ([P, c_int, P, P, P], c_int),
+        "vie_rooftop_solve": ([P, P, P, c_double, c_int32, c_double, P, POINTER(SolveStats)], c_int),
+        "vie_rooftop_far_field_rcs": ([P, P, c_int32, POINTER(c_double), POINTER(c_double), P], c_int),
         "vie_set_device_budget": ([c_int64], c_int),
         "vie_device_usage": ([POINTER(c_int64), POINTER(c_int64)], c_int),
         "vie_fault_inject_alloc": ([c_int32], c_int),
@@ -327,6 +333,62 @@ class Grid:
         out_host.copy_(e, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return out_host, st
+
+
+class Rooftop:
+    """The paper's rooftop / pulse discretisation of a grid's permittivity (vie_rooftop): unknown
+    w = J / (j w eps0) on faces, vectors (3, nz, ny, nx) with component a at the face above cell c."""
+
+    def __init__(self, grid, k0, precision=C128 | C64):
+        self.grid = grid
+        self.k0 = float(k0)
+        h = c_void_p()
+        _check(load().vie_rooftop_create(grid.handle, self.k0, int(precision), _stream(), byref(h)))
+        self.handle = h
+
+    def incident(self, khat, pol, precision=C128):
+        out = self.grid.empty(precision)
+        kh = (c_double * 3)(*[float(v) for v in khat])
+        p = np.asarray(pol, dtype=np.complex128)
+        pv = (c_double * 6)(p[0].real, p[0].imag, p[1].real, p[1].imag, p[2].real, p[2].imag)
+        _check(load().vie_rooftop_incident(self.handle, kh, pv, precision, self.grid._vec(out, precision, "out"),
+                                           _stream()))
+        return out
+
+    def matvec(self, w, y=None):
+        precision = C128 if w.dtype == _dtype(C128) else C64
+        y = self.grid.empty(precision) if y is None else y
+        _check(load().vie_rooftop_matvec(self.handle, precision, self.grid._vec(w, precision, "w"),
+                                         self.grid._vec(y, precision, "y"), _stream()))
+        return y
+
+    def solve(self, b, w=None, tol=1e-6, maxit=1000, wait_timeout_ms=0.0, check=True):
+        w = self.grid.empty(C128) if w is None else w
+        st = SolveStats()
+        rc = load().vie_rooftop_solve(self.handle, self.grid._vec(b, C128, "b"), self.grid._vec(w, C128, "w"),
+                                      float(tol), int(maxit), float(wait_timeout_ms), _stream(), byref(st))
+        if check:
+            _check(rc, allow=(VIE_ENOTCONV,))
+        return w, _struct_dict(st)
+
+    def far_field_rcs(self, w, dirs):
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
+        out = np.empty(d.shape[0], dtype=np.float64)
+        _check(load().vie_rooftop_far_field_rcs(self.handle, self.grid._vec(w, C128, "w"), d.shape[0],
+                                                d.ctypes.data_as(POINTER(c_double)),
+                                                out.ctypes.data_as(POINTER(c_double)), _stream()))
+        return out
+
+    def close(self):
+        if self.handle:
+            _check(load().vie_rooftop_release(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
