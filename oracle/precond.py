@@ -14,8 +14,8 @@ Pinned by tests/test_oracle_solver.py: against dense per-block LU, and the
 single-block case where K2 = A exactly (the outer solve then converges at its
 first half-step).
 
-Expanded blocks (the paper's conclusion names "expanded blocks containing more
-field information" as future work; the reading taken here): with expand = e > 0
+Expanded blocks (the paper's conclusion names enlarged blocks that carry more of
+the surrounding field as future work; the reading taken here): with expand = e > 0
 block k is solved on S_k+ = S_k plus every voxel with chi != 0 within Chebyshev
 distance e of S_k (other blocks' voxels included), and only the values on S_k
 are kept (restricted additive Schwarz). Air voxels of the halo are left out:
