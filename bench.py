@@ -51,14 +51,18 @@ def parse():
                          "(complex64, incident field; the 4th is profiled and its statistics printed), full-grid "
                          "complex64 MVMs or mixed solves, and exit")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--serve", type=int, default=8, help="requests in the serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate, requests/s")
-    ap.add_argument("--serve-sizes", default="32,64", help="cubic grid sizes of the serving stream")
-    ap.add_argument("--serve-kinds", default="metasurface",
+    ap.add_argument("--serve", type=int, default=0, help="requests in a single Poisson serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate of --serve, requests/s")
+    ap.add_argument("--serve-sizes", default="32,64,96,128", help="cubic grid sizes of the serving stream")
+    ap.add_argument("--serve-weights", default="0.4,0.3,0.2,0.1", help="draw probabilities of --serve-sizes")
+    ap.add_argument("--serve-kinds", default="metasurface,solar_cell",
                     help="structures of the serving stream: metasurface and/or solar_cell (comma separated)")
-    ap.add_argument("--serve-sweep", default="",
-                    help="comma-separated fractions of the measured saturation rate for a latency sweep (off by default)")
-    ap.add_argument("--serve-sweep-requests", type=int, default=24, help="requests per sweep point")
+    ap.add_argument("--serve-modes", default="mixed,fp64",
+                    help="solve modes of the serving sweep: mixed (complex64 block solves, FP64 residuals) and/or "
+                         "fp64 (complex128 throughout, block preconditioner too)")
+    ap.add_argument("--serve-sweep", default="0.25,0.5,0.75,1.0,1.25",
+                    help="comma-separated fractions of the measured saturation rate for the latency sweep ('' skips)")
+    ap.add_argument("--serve-sweep-requests", type=int, default=16, help="requests per sweep point")
     ap.add_argument("--block-sweep", default="",
                     help="comma-separated metasurface block divisions for a Table 2 style sweep: 0 = one block per "
                          "pillar, m > 0 = m x m unit cells per block, air included (off by default)")
@@ -295,6 +299,102 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def run_serving(args, rank):
+    """Serving (config c5): Poisson arrivals through serve.Server, continuous batching over slots (p50/p99
+    latency), mixed and FP64 modes, merged and separate block-solver launches; the per-result error
+    against the oracle on the sampled requests. Returns (serving, serving_sweep)."""
+    import torch
+    from paper_2501_13512_gb300 import vie
+    # serving: Poisson arrivals, continuous batching over slots (p50/p99 latency), mixed and FP64 modes
+    serving = None
+    serving_sweep = None
+    if args.serve > 0 or args.serve_sweep:
+        from paper_2501_13512_gb300 import serve
+        sizes = tuple(int(v) for v in args.serve_sizes.split(","))
+        wts = tuple(float(v) for v in args.serve_weights.split(","))
+        kinds = tuple(args.serve_kinds.split(","))
+        modes = {"mixed": vie.MODE_MIXED, "fp64": vie.MODE_PLAIN_C128}
+        workload = (f"{'/'.join(kinds)} structures on n^3 grids, n in {list(sizes)} drawn with weights {list(wts)}, "
+                    "h = 10 nm, wavelengths 400-800 nm (10 nm grid), incidence U[0, 30 deg]; block-preconditioned, "
+                    "outer 1e-6 (FP64 true residual), inner 1e-2, outer_maxit 400; 4 slots")
+        budget = int(0.5 * torch.cuda.get_device_properties(0).total_memory)
+
+        def serve_run(reqs, rate, seed, want_field=False, merge=True):
+            """One request stream through a fresh server; rate None = all requests at once. merge: concurrent
+            requests' block solves share persistent launches (vie_solve_merged)."""
+            for r in reqs:
+                r.want_field = want_field
+            srv = serve.Server(budget_bytes=budget, slots=4, merge=merge)
+            rng = np.random.default_rng(1 + seed)
+            futs = []
+            try:
+                for r in reqs:
+                    futs.append(srv.submit(r))
+                    if rate:
+                        time.sleep(rng.exponential(1.0 / rate))
+                res = [f.result(timeout=900) for f in futs]
+                mstats = srv.engine.merge_stats()
+            finally:
+                srv.close()
+            slat = np.array([x.latency_s for x in res])
+            st = srv.latency_stats()
+            return {"requests": len(res), "arrival_rate": rate,
+                    "p50_s": float(np.percentile(slat, 50)), "p99_s": float(np.percentile(slat, 99)),
+                    "solves_per_s": st["solves_per_s"], "p50_s_by_size": st["p50_s_by_size"],
+                    "converged": int(sum(x.stats["status"] == 0 for x in res)),
+                    "max_true_rel_res": float(max(x.stats["true_rel_res"] for x in res)),
+                    "outer_iters": [x.stats["outer_iters"] for x in res],
+                    "merged_launches": mstats, "cache": dict(srv.engine.hits)}, res
+
+        def stream(n, seed, mode):
+            return serve.make_stream(n, seed=seed, sizes=sizes, weights=wts, kinds=kinds, outer_maxit=400, mode=mode)
+
+        if args.serve > 0:
+            serving, _ = serve_run(stream(args.serve, rank, vie.MODE_MIXED), args.serve_rate, rank)
+            serving["workload"] = workload
+        if args.serve_sweep:
+            # per mode: saturation (every request submitted at once), then Poisson streams at fractions of
+            # it; the same seeded problems in both modes
+            n = args.serve_sweep_requests
+            serving_sweep = {"workload": workload, "requests_per_point": n, "slots": 4}
+            for name in args.serve_modes.split(","):
+                sat, _ = serve_run(stream(n, 100 + rank, modes[name]), None, 100 + rank)
+                rows = []
+                for f in (float(v) for v in args.serve_sweep.split(",")):
+                    r, _ = serve_run(stream(n, 200 + rank, modes[name]), f * sat["solves_per_s"], 200 + rank)
+                    r["fraction_of_saturation"] = f
+                    rows.append(r)
+                serving_sweep[name] = {"saturation": sat, "rates": rows}
+                serving_sweep[f"solves_per_s_{name}"] = sat["solves_per_s"]
+                # the same saturation stream with every request's block solves in launches of its own
+                unmerged, _ = serve_run(stream(n, 100 + rank, modes[name]), None, 100 + rank, merge=False)
+                serving_sweep[name]["saturation_unmerged"] = unmerged
+            # per-result error against the oracle on the sampled requests (stored oracle solves to 1e-10)
+            gpath = os.path.join(ROOT, "tests", "golden", "serve_requests.npz")
+            if os.path.exists(gpath):
+                gd = np.load(gpath)
+                metas = [json.loads(str(gd[f"meta_{i}"])) for i in range(3)]
+                sampled = []
+                for name in args.serve_modes.split(","):
+                    reqs = serve.make_stream(4, seed=1, sizes=(32, 64), weights=(0.4, 0.3),
+                                             kinds=("metasurface", "solar_cell"), outer_maxit=400, mode=modes[name])
+                    reqs = [reqs[m["request"]] for m in metas]
+                    _, res = serve_run(reqs, None, 300, want_field=True)
+                    for i, (m, x) in enumerate(zip(metas, res)):
+                        idx, ref = gd[f"index_{i}"], gd[f"value_{i}"]
+                        got = x.field.ravel()[idx]
+                        sampled.append({"mode": name, "request": m["structure"], "lambda_nm": m["lambda_nm"],
+                                        "true_rel_res": x.stats["true_rel_res"],
+                                        "rel_field_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))})
+                serving_sweep["sampled_vs_oracle"] = sampled
+                serving_sweep["sampled_note"] = ("3 sampled requests (32^3 and 64^3 metasurface tiles, 32^3 solar "
+                                                 "cell; inputs.serving_draws seed 1) served together in each mode; "
+                                                 "error at 8192 "
+                                                 "seeded entries against the oracle solved to 1e-10 "
+                                                 "(tests/golden/serve_requests.npz)")
+    return serving, serving_sweep
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -506,57 +606,7 @@ def main():
     else:
         kernels = None
 
-    # serving: Poisson arrivals, continuous batching over slots (p50/p99 latency)
-    serving = None
-    serving_sweep = None
-    if args.serve > 0 or args.serve_sweep:
-        from paper_2501_13512_gb300 import serve
-        sizes = tuple(int(v) for v in args.serve_sizes.split(","))
-        wts = [serve.SIZE_WEIGHTS[serve.SIZES.index(n)] if n in serve.SIZES else 1.0 for n in sizes]
-        kinds = tuple(args.serve_kinds.split(","))
-        workload = (f"{'/'.join(kinds)} structures on n^3 grids (n in {list(sizes)}), h = 10 nm, wavelengths "
-                    "400-800 nm (10 nm grid), random incidence; mixed, outer 1e-6, inner 1e-2, outer_maxit 400")
-        budget = int(0.5 * torch.cuda.get_device_properties(0).total_memory)
-
-        def serve_run(nreq, rate, seed):
-            """One request stream through a fresh server; rate None = all requests at once."""
-            reqs = serve.make_stream(nreq, seed=seed, sizes=sizes, weights=wts, kinds=kinds, outer_maxit=400)
-            for r in reqs:
-                r.want_field = False
-            srv = serve.Server(budget_bytes=budget, slots=4)
-            rng = np.random.default_rng(1 + seed)
-            futs = []
-            try:
-                for r in reqs:
-                    futs.append(srv.submit(r))
-                    if rate:
-                        time.sleep(rng.exponential(1.0 / rate))
-                res = [f.result(timeout=600) for f in futs]
-            finally:
-                srv.close()
-            slat = np.array([x.latency_s for x in res])
-            st = srv.latency_stats()
-            return {"requests": len(res), "arrival_rate": rate, "sizes": list(sizes), "slots": 4,
-                    "p50_s": float(np.percentile(slat, 50)), "p99_s": float(np.percentile(slat, 99)),
-                    "solves_per_s": st["solves_per_s"],
-                    "converged": int(sum(x.stats["status"] == 0 for x in res)),
-                    "max_true_rel_res": float(max(x.stats["true_rel_res"] for x in res)),
-                    "cache": dict(srv.engine.hits)}
-
-        if args.serve > 0:
-            serving = serve_run(args.serve, args.serve_rate, rank)
-            serving["workload"] = workload
-        if args.serve_sweep:
-            # saturation: every request submitted at once; then Poisson streams at fractions of it
-            n = args.serve_sweep_requests
-            sat = serve_run(n, None, 100 + rank)
-            rows = []
-            for f in (float(v) for v in args.serve_sweep.split(",")):
-                r = serve_run(n, f * sat["solves_per_s"], 200 + rank)
-                r["fraction_of_saturation"] = f
-                rows.append(r)
-            serving_sweep = {"saturation_solves_per_s": sat["solves_per_s"], "saturation": sat, "rates": rows,
-                             "workload": workload}
+    serving, serving_sweep = run_serving(args, rank)
 
     # block-division sweep (Table 2's trade-off): blocks vs outer iterations vs time, one solve each
     block_sweep = None

@@ -241,6 +241,63 @@ int vie_solve(vie_grid* grid, const vie_spectrum* spectrum, const void* einc_dev
               void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
               vie_solve_stats* stats);
 
+/* ---- Solves of many requests with merged block-solver launches. ----
+ * Serving runs the solves of several requests at once, each on its own grid
+ * (any shapes, modes and tolerances), host thread and stream. Inside a merge
+ * session, every block-preconditioner application (Eq. 10) of a solve first
+ * gathers its blocks and then waits (on the host) until every other solve of
+ * the session that still applies a preconditioner has reached its next
+ * application; their blocks then run in ONE persistent launch (one per
+ * precision, inner tolerance and inner limit), the longest-running blocks
+ * first. Merged are the blocks that the persistent block solver takes for
+ * their grid alone (VIE_GRID_AUTO: grids with 32 or more fitting blocks) and
+ * the complex64 blocks of its on-chip slab MVM (every padded axis in [8, 32]);
+ * the other blocks run in their grid's batched launches meanwhile. A solve joins at its first application
+ * and leaves when it stops applying the preconditioner, so requests that arrive
+ * while others run share launches from then on (continuous batching). Each
+ * solve runs exactly the iteration of vie_solve; its result equals the
+ * vie_solve result up to rounding (the merged launches use clusters of 2 CTAs
+ * per block, while vie_solve tunes the cluster size per grid). */
+typedef struct vie_merge_session vie_merge_session;
+
+typedef struct {
+    int32_t launches;        /* merged persistent block-solver launches queued     */
+    int32_t max_solves;      /* most solves whose blocks shared one launch         */
+    double mean_solves;      /* solves per launch, averaged over the launches      */
+} vie_merge_stats;
+
+/* Creates a session on the current device (it owns a stream and the work
+ * lists of the merged launches). Errors: VIE_EINVAL, VIE_ECUDA. */
+int vie_merge_session_create(vie_merge_session** out);
+
+/* Frees the session after its queued launches. VIE_EBUSY while a
+ * vie_solve_merged call is running in it (nothing is freed then). */
+int vie_merge_session_destroy(vie_merge_session* session);
+
+/* The session's merged launches so far. */
+int vie_merge_session_stats(vie_merge_session* session, vie_merge_stats* out);
+
+/* vie_solve inside a session: same arguments, results and errors as vie_solve
+ * (blocking; call it from one host thread per solve, with its own stream and
+ * its own grid). A grid must not be in two running solves at once. */
+int vie_solve_merged(vie_merge_session* session, vie_grid* grid, const vie_spectrum* spectrum,
+                     const void* einc_dev, void* e_dev, const vie_solve_opts* opts,
+                     vie_stream_t stream, vie_solve_stats* stats);
+
+/* n solves at once in a session of their own (all members from the first
+ * application on), one internal host thread and stream each; returns when all
+ * have finished, their work ordered after the work queued on `stream` before
+ * the call and before work queued on it after. grids[n]: distinct grids;
+ * spectra[n], einc_dev[n], e_dev[n], opts[n]: as for vie_solve, per solve.
+ * stats[n] (may be NULL): per solve, status = that solve's return code.
+ * merge (may be NULL): the session's merged launches. n = 1 is vie_solve.
+ * Returns VIE_OK when every solve returned VIE_OK, else the code of the first
+ * solve (by index) that did not, with its message; VIE_EINVAL for n < 1, a
+ * null array or a grid listed twice (nothing runs then). */
+int vie_solve_many(int32_t n, vie_grid* const* grids, const vie_spectrum* const* spectra,
+                   const void* const* einc_dev, void* const* e_dev, const vie_solve_opts* opts,
+                   vie_stream_t stream, vie_solve_stats* stats, vie_merge_stats* merge);
+
 /* ---- Batched independent solves (many instances of one grid shape). ---- */
 typedef struct vie_batch vie_batch;
 

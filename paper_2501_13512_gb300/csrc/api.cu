@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <condition_variable>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -487,6 +488,13 @@ extern "C" int vie_grid_create(const vie_grid_desc* d, vie_grid** out) {
             if (inner_persistent_ok(gr.bs, es, true)) fit_blocks += gr.bs.nb;
         const bool force = d->flags == VIE_GRID_INNER_PERSISTENT || fit_blocks >= kInnerMinBlocks;
         for (auto& gr : g->groups) {
+            // merged launches across grids take the blocks the persistent solver would take here, and
+            // complex64 blocks of the on-chip slab MVM (a few such blocks of one grid iterate faster in
+            // the batched launches, which spread each block over the whole GPU, but many of them, from
+            // several grids, fill the GPU in one launch; larger boxes stay batched)
+            gr.fit[prec] = d->flags != VIE_GRID_INNER_BATCHED && inner_persistent_ok(gr.bs, es, true) &&
+                           (force || (prec == 1 && slab_path_ok(gr.bs, es) && !slab_disabled()));
+            gr.last_iters[prec].assign(gr.bs.nb, 0.f);
             bool ok = d->flags != VIE_GRID_INNER_BATCHED && inner_persistent_ok(gr.bs, es, force);
             (prec == 0 ? gr.persistent128 : gr.persistent64) = ok;
             if (!ok) continue;
@@ -729,11 +737,213 @@ static int mvm_full(vie_grid* g, const vie_spectrum* sp, const C* x, C* y, cudaS
     return mvm_boxes<C>(g->full, spec_of<C>(sp, 0), x, y, nullptr, s);
 }
 
+// ---------------------------------------------------------------- merged block-solver launches
+// Solves that run at the same time, one host thread and one stream each, inside one merge
+// session (vie_solve_merged, vie_solve_many). A preconditioner application queues its gathers on
+// its own stream and arrives here; once every solve of the session that still applies a
+// preconditioner has arrived, the last one to arrive queues ONE persistent launch over the blocks
+// of all of them (one per precision, inner tolerance and iteration limit) on the session's merge
+// stream. Each solve's stream then waits for that launch before its blocks are scattered back.
+// Each block's work is the same as in a launch of its grid alone.
+struct MergeReq {
+    vie_grid* g = nullptr;
+    const vie_spectrum* sp = nullptr;
+    int prec = 0;                  // 0: complex128, 1: complex64
+    double tol = 0.0;
+    int maxit = 0;
+    cudaEvent_t ready = nullptr;   // recorded on the solve's stream after its gathers
+    int64_t gen = -1;              // launch that took it (-1: none yet, -2: that launch failed)
+};
+
+struct MergeLaunch {
+    cudaEvent_t done = nullptr;
+    int waiting = 0;               // members that have not yet made their stream wait for it
+};
+
+}  // namespace vie
+
+struct vie_merge_session {
+    std::mutex m;
+    std::condition_variable cv;
+    int device = 0;
+    int live = 0;                  // solves that may still arrive
+    int inside = 0;                // solves inside the session
+    std::vector<vie::MergeReq*> pending;
+    cudaStream_t ms = nullptr;     // every merged launch, in order
+    std::map<int64_t, vie::MergeLaunch> launches_open;
+    std::vector<cudaEvent_t> free_events;
+    int64_t next_gen = 0;
+    char* d_groups = nullptr;      // group descriptors of a launch
+    int2* d_work = nullptr;        // (job, box) work list of a launch
+    int* d_next = nullptr;
+    int64_t groups_cap = 0, work_cap = 0;
+    std::vector<void*> retired;    // outgrown buffers (a queued launch may still read them)
+    int launches = 0;
+    int64_t members = 0;
+    int max_members = 0;
+    std::string err;
+};
+
+namespace vie {
+
+using MergeCtx = vie_merge_session;
+
+// One solve's membership: it leaves (once) when it stops applying the preconditioner.
+struct MergeMember {
+    MergeCtx* ctx = nullptr;
+    bool live = false;
+};
+
+static int merge_capacity(MergeCtx* mc, int64_t ngroups, int64_t nwork) {
+    if (ngroups > mc->groups_cap) {
+        char* p = nullptr;
+        const int64_t cap = std::max<int64_t>(ngroups, 2 * mc->groups_cap);
+        VIE_TRY(dmalloc((void**)&p, cap * inner_group_desc_bytes(), "merged block-solver launch"));
+        if (mc->d_groups) mc->retired.push_back(mc->d_groups);
+        mc->d_groups = p;
+        mc->groups_cap = cap;
+    }
+    if (nwork > mc->work_cap) {
+        int2* p = nullptr;
+        const int64_t cap = std::max<int64_t>(nwork, 2 * mc->work_cap);
+        VIE_TRY(dmalloc((void**)&p, cap * sizeof(int2), "merged block-solver launch"));
+        if (mc->d_work) mc->retired.push_back(mc->d_work);
+        mc->d_work = p;
+        mc->work_cap = cap;
+    }
+    if (!mc->d_next) VIE_TRY(dmalloc((void**)&mc->d_next, 2 * sizeof(int), "merged block-solver launch"));
+    return VIE_OK;
+}
+
+template <class C>
+static int merged_launch(MergeCtx* mc, const std::vector<MergeReq*>& reqs) {
+    const int pi = prec_of<C>() == VIE_C128 ? 0 : 1;
+    std::vector<InnerJob<C>> jobs;
+    std::vector<std::pair<double, int2>> items;
+    for (MergeReq* r : reqs) {
+        vie_grid* g = r->g;
+        for (size_t i = 0; i < g->groups.size(); ++i) {
+            Group& gr = g->groups[i];
+            if (!gr.fit[pi]) continue;
+            InnerJob<C> j;
+            j.bs = &gr.bs;
+            j.v = group_vecs<C>(gr);
+            j.chi = chi_of<C>(gr.bs);
+            j.G = spec_of<C>(r->sp, 1 + (int)i);
+            j.st = gr.st;
+            if (pi == 1 && !slab_disabled()) j.Go = reinterpret_cast<const C*>(r->sp->go64[1 + i]);
+            const int job = (int)jobs.size();
+            jobs.push_back(j);
+            // longest first: the block's iterations in its last application x its padded box size
+            for (int b = 0; b < gr.bs.nb; ++b)
+                items.push_back({(gr.last_iters[pi][b] + 1.0) * (double)gr.bs.spec_elems(), make_int2(job, b)});
+        }
+    }
+    if (jobs.empty()) return VIE_OK;
+    VIE_TRY(merge_capacity(mc, (int64_t)jobs.size(), (int64_t)items.size()));
+    std::stable_sort(items.begin(), items.end(), [](const std::pair<double, int2>& a, const std::pair<double, int2>& b) {
+        return a.first > b.first;
+    });
+    std::vector<int2> w(items.size());
+    for (size_t k = 0; k < items.size(); ++k) w[k] = items[k].second;
+    VIE_CK(cudaMemcpyAsync(mc->d_work, w.data(), w.size() * sizeof(int2), cudaMemcpyHostToDevice, mc->ms));
+    return inner_persistent<C>(jobs, mc->d_work, (int)w.size(), mc->d_groups, mc->d_next, reqs[0]->tol,
+                               reqs[0]->maxit, mc->ms, 2, nullptr);
+}
+
+// Called with mc->m held: one launch per (precision, tolerance, limit) over every pending request.
+static void merge_flush(MergeCtx* mc) {
+    std::vector<MergeReq*> reqs;
+    reqs.swap(mc->pending);
+    std::stable_sort(reqs.begin(), reqs.end(), [](const MergeReq* a, const MergeReq* b) {
+        return std::tie(a->prec, a->tol, a->maxit) < std::tie(b->prec, b->tol, b->maxit);
+    });
+    for (size_t i = 0; i < reqs.size();) {
+        size_t j = i;
+        while (j < reqs.size() && reqs[j]->prec == reqs[i]->prec && reqs[j]->tol == reqs[i]->tol &&
+               reqs[j]->maxit == reqs[i]->maxit)
+            ++j;
+        std::vector<MergeReq*> part(reqs.begin() + i, reqs.begin() + j);
+        int rc = VIE_OK;
+        for (MergeReq* r : part) {
+            cudaError_t e = cudaStreamWaitEvent(mc->ms, r->ready, 0);
+            if (e != cudaSuccess && !rc) rc = cuda_fail(e, "cudaStreamWaitEvent(merge)", __FILE__, __LINE__);
+        }
+        if (!rc) rc = part[0]->prec == 0 ? merged_launch<double2>(mc, part) : merged_launch<float2>(mc, part);
+        cudaEvent_t ev = nullptr;
+        if (!rc) {
+            cudaError_t e = cudaSuccess;
+            if (!mc->free_events.empty()) {
+                ev = mc->free_events.back();
+                mc->free_events.pop_back();
+            } else {
+                e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev, mc->ms);
+            if (e != cudaSuccess) rc = cuda_fail(e, "merge event", __FILE__, __LINE__);
+        }
+        if (rc) {
+            if (mc->err.empty()) mc->err = g_last_error;
+            if (ev) mc->free_events.push_back(ev);
+            for (MergeReq* r : part) r->gen = -2;
+        } else {
+            const int64_t gen = mc->next_gen++;
+            mc->launches_open[gen] = MergeLaunch{ev, (int)part.size()};
+            for (MergeReq* r : part) r->gen = gen;
+            mc->launches++;
+            mc->members += (int64_t)part.size();
+            mc->max_members = std::max(mc->max_members, (int)part.size());
+        }
+        i = j;
+    }
+    mc->cv.notify_all();
+}
+
+static void merge_join(MergeMember* mm) {
+    MergeCtx* mc = mm->ctx;
+    std::lock_guard<std::mutex> lock(mc->m);
+    mc->live++;
+    mm->live = true;
+}
+
+static void merge_arrive(MergeMember* mm, MergeReq* r) {
+    MergeCtx* mc = mm->ctx;
+    std::lock_guard<std::mutex> lock(mc->m);
+    mc->pending.push_back(r);
+    if ((int)mc->pending.size() >= mc->live) merge_flush(mc);
+}
+
+// Waits (on the host) until the launch holding r is queued; the solve's stream then waits for it.
+static int merge_wait(MergeMember* mm, MergeReq* r, cudaStream_t s) {
+    MergeCtx* mc = mm->ctx;
+    std::unique_lock<std::mutex> lock(mc->m);
+    mc->cv.wait(lock, [&] { return r->gen != -1; });
+    if (r->gen == -2) return fail(VIE_ECUDA, "merged block-solver launch failed: " + mc->err);
+    auto it = mc->launches_open.find(r->gen);
+    cudaError_t e = cudaStreamWaitEvent(s, it->second.done, 0);
+    if (--it->second.waiting == 0) {       // the event may be recorded again by a later launch
+        mc->free_events.push_back(it->second.done);
+        mc->launches_open.erase(it);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent(merged launch)", __FILE__, __LINE__);
+    return VIE_OK;
+}
+
+static void merge_leave(MergeMember* mm) {
+    if (!mm || !mm->live) return;
+    MergeCtx* mc = mm->ctx;
+    std::lock_guard<std::mutex> lock(mc->m);
+    mm->live = false;
+    mc->live--;
+    if (!mc->pending.empty() && (int)mc->pending.size() >= mc->live) merge_flush(mc);
+}
+
 // y = K2^{-1} b: all blocks of all groups iterate together; a block stops
 // when its own residual meets tol (or at maxit) and is skipped thereafter.
 template <class C>
 static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, double tol, int maxit,
-                         cudaStream_t s, vie_precond_stats* stats, double timeout_ms) {
+                         cudaStream_t s, vie_precond_stats* stats, double timeout_ms,
+                         MergeMember* mm = nullptr) {
     const int64_t n3 = 3 * g->N;
     if (stats) memset(stats, 0, sizeof(*stats));
     if (g->nblocks == 0) return vec_copy<C>(b, y, n3, s);
@@ -741,11 +951,17 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     const bool c128 = prec_of<C>() == VIE_C128;
     std::vector<InnerJob<C>> jobs;
     std::vector<int> batched;
+    const bool merged = mm != nullptr && mm->live;
+    bool any_fit = false;
     for (int i = 0; i < ng; ++i) {
         Group& gr = g->groups[i];
         KrylovVecs<C>& v = group_vecs<C>(gr);
         VIE_TRY(precond_gather<C>(g, gr, b, v.b, s));
-        if (c128 ? gr.persistent128 : gr.persistent64) {
+        if (merged) {
+            // blocks that fit the persistent solver go to the merged launch, the rest run here
+            if (gr.fit[c128 ? 0 : 1]) any_fit = true;
+            else batched.push_back(i);
+        } else if (c128 ? gr.persistent128 : gr.persistent64) {
             InnerJob<C> j;
             j.bs = &gr.bs;
             j.v = v;
@@ -763,6 +979,29 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     // applies; then the best. Register-FFT MVM: 2, 4, split 4/2. Slab MVM (whole MVM on chip, the
     // cluster splits the kz planes): 2, 1, 4 (a split cannot shorten the slowest block's solve, which
     // bounds the apply once every block fits on the device at once).
+    // after arriving, the request is waited for on every path out of this function
+    if (merged && !any_fit) merge_leave(mm);   // nothing of this grid fits: do not hold the others
+    MergeReq req;
+    struct Guard {
+        MergeMember* mm;
+        MergeReq* r;
+        cudaStream_t s;
+        bool armed = false;
+        ~Guard() {
+            if (armed) merge_wait(mm, r, s);
+        }
+    } guard{mm, &req, s};
+    if (merged && any_fit) {
+        VIE_CK(cudaEventRecord(g->fork_ev, s));
+        req.g = g;
+        req.sp = sp;
+        req.prec = c128 ? 0 : 1;
+        req.tol = tol;
+        req.maxit = maxit;
+        req.ready = g->fork_ev;
+        merge_arrive(mm, &req);
+        guard.armed = true;
+    }
     bool slab = false;
     for (const InnerJob<C>& j : jobs) slab = slab || j.Go != nullptr;
     static const int kCand[3] = {2, 4, -1};
@@ -834,11 +1073,15 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
         VIE_CK(cudaEventRecord(g->join_ev, g->s2));
         VIE_CK(cudaStreamWaitEvent(s, g->join_ev, 0));
     }
+    if (guard.armed) {
+        guard.armed = false;
+        VIE_TRY(merge_wait(mm, &req, s));
+    }
     VIE_TRY(precond_copy_unblocked<C>(g, b, y, s));
     for (int i = 0; i < ng; ++i) VIE_TRY(precond_scatter_group<C>(g, g->groups[i], group_vecs<C>(g->groups[i]).x, y, s));
     std::vector<int2>& wh = g->work_host[c128 ? 0 : 1];
     const bool reorder = !jobs.empty() && wh.size() > 1;
-    if (stats || reorder) {
+    if (stats || reorder || merged) {
         std::vector<std::vector<SegState>> hs(ng);
         for (int i = 0; i < ng; ++i) {
             Group& gr = g->groups[i];
@@ -847,6 +1090,8 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
         }
         VIE_CK(cudaEventRecord(g->ev[0], s));
         VIE_TRY(wait_event(g->ev[0], timeout_ms));
+        for (int i = 0; i < ng; ++i)
+            for (int k = 0; k < g->groups[i].bs.nb; ++k) g->groups[i].last_iters[c128 ? 0 : 1][k] = (float)hs[i][k].iters;
         if (stats) {
             double sum = 0.0;
             stats->nblocks = g->nblocks;
@@ -935,7 +1180,8 @@ struct SolveAccum {
 // y = K2^{-1} p and z = K2^{-1} s each iteration, x updated with the y, z computed.
 template <class C>
 static int bicgstab_full(vie_grid* g, const vie_spectrum* sp, KrylovVecs<C> v, const vie_solve_opts* o,
-                         double tol, int maxit, cudaStream_t s, SolveAccum& acc, SegState* final_state) {
+                         double tol, int maxit, cudaStream_t s, SolveAccum& acc, SegState* final_state,
+                         MergeMember* mm) {
     const bool pre = o->use_precond && g->nblocks > 0;
     if (!pre) {
         v.y = v.p;
@@ -952,7 +1198,7 @@ static int bicgstab_full(vie_grid* g, const vie_spectrum* sp, KrylovVecs<C> v, c
     VIE_TRY(read_outer_state(g, &hs, s, o->wait_timeout_ms));
     vie_precond_stats ps;
     auto precond = [&](const C* in, C* outv) -> int {
-        VIE_TRY(precond_apply<C>(g, sp, in, outv, o->inner_tol, o->inner_maxit, s, &ps, o->wait_timeout_ms));
+        VIE_TRY(precond_apply<C>(g, sp, in, outv, o->inner_tol, o->inner_maxit, s, &ps, o->wait_timeout_ms, mm));
         acc.precond_applies++;
         acc.inner_iters += (int64_t)std::llround(ps.mean_iters * ps.nblocks);
         return VIE_OK;
@@ -1041,8 +1287,19 @@ extern "C" int vie_block_precond_apply(vie_grid* g, const vie_spectrum* sp, int 
     return wait_event(g->ev[0], 0);
 }
 
+namespace vie {
+static int solve_impl(vie_grid* g, const vie_spectrum* sp, const void* einc, void* e, const vie_solve_opts* o,
+                      cudaStream_t stream, vie_solve_stats* stats, MergeMember* mm);
+}
+
 extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, void* e, const vie_solve_opts* o,
                          vie_stream_t stream, vie_solve_stats* stats) {
+    return solve_impl(g, sp, einc, e, o, (cudaStream_t)stream, stats, nullptr);
+}
+
+namespace vie {
+static int solve_impl(vie_grid* g, const vie_spectrum* sp, const void* einc, void* e, const vie_solve_opts* o,
+                      cudaStream_t stream, vie_solve_stats* stats, MergeMember* mm) {
     if (!g || !einc || !e || !o) return fail(VIE_EINVAL, "vie_solve: null argument");
     VIE_TRY(check_spectrum(g, sp, VIE_C128));
     if (o->mode == VIE_MODE_MIXED) VIE_TRY(check_spectrum(g, sp, VIE_C64));
@@ -1089,7 +1346,7 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
             tol = rel0 > 0 ? o->outer_tol / rel0 : o->outer_tol;
         }
         SegState fs;
-        VIE_TRY(bicgstab_full<double2>(g, sp, v, o, tol, o->outer_maxit, s, acc, &fs));
+        VIE_TRY(bicgstab_full<double2>(g, sp, v, o, tol, o->outer_maxit, s, acc, &fs, mm));
         st.outer_iters = fs.iters;
         rc = status_code(fs.status);
         if (x0) VIE_TRY(vec_sum128(x0, v.x, x, n3, s));
@@ -1128,6 +1385,7 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
                         break;
                     }
                     oc.use_precond = 0;
+                    merge_leave(mm);
                 }
             }
             if (rel <= o->outer_tol) {
@@ -1144,7 +1402,7 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
             VIE_TRY(vec_scale_to_c64(g->o128.r, g->dscal + 1, g->o64.b, n3, s));
             const double eta = std::max(0.5 * o->outer_tol / rel, 1e-4);
             SegState fs;
-            VIE_TRY(bicgstab_full<float2>(g, sp, g->o64, &oc, std::min(eta, 0.5), o->outer_maxit, s, acc, &fs));
+            VIE_TRY(bicgstab_full<float2>(g, sp, g->o64, &oc, std::min(eta, 0.5), o->outer_maxit, s, acc, &fs, mm));
             st.outer_iters += fs.iters;
             if (fs.status == SEG_BREAKDOWN && fs.iters == 0) {
                 rc = VIE_EBREAKDOWN;
@@ -1168,4 +1426,171 @@ extern "C" int vie_solve(vie_grid* g, const vie_spectrum* sp, const void* einc, 
         if (rc == VIE_EBREAKDOWN) set_error("vie_solve: BiCGSTAB breakdown");
     }
     return rc;
+}
+
+}  // namespace vie
+
+// ---------------------------------------------------------------- merge sessions
+extern "C" int vie_merge_session_create(vie_merge_session** out) {
+    if (!out) return fail(VIE_EINVAL, "vie_merge_session_create: null argument");
+    *out = nullptr;
+    auto* mc = new vie_merge_session();
+    VIE_CK(cudaGetDevice(&mc->device));
+    cudaError_t e = cudaStreamCreateWithFlags(&mc->ms, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete mc;
+        return cuda_fail(e, "vie_merge_session_create: stream", __FILE__, __LINE__);
+    }
+    *out = mc;
+    return VIE_OK;
+}
+
+extern "C" int vie_merge_session_destroy(vie_merge_session* mc) {
+    if (!mc) return fail(VIE_EINVAL, "vie_merge_session_destroy: null session");
+    {
+        std::lock_guard<std::mutex> lock(mc->m);
+        if (mc->inside > 0) return fail(VIE_EBUSY, "vie_merge_session_destroy: solves are still running in the session");
+    }
+    cudaStreamSynchronize(mc->ms);
+    cudaStreamDestroy(mc->ms);
+    for (auto& kv : mc->launches_open) cudaEventDestroy(kv.second.done);
+    for (auto ev : mc->free_events) cudaEventDestroy(ev);
+    for (void* p : mc->retired) dfree(p);
+    dfree(mc->d_groups);
+    dfree(mc->d_work);
+    dfree(mc->d_next);
+    delete mc;
+    return VIE_OK;
+}
+
+extern "C" int vie_merge_session_stats(vie_merge_session* mc, vie_merge_stats* out) {
+    if (!mc || !out) return fail(VIE_EINVAL, "vie_merge_session_stats: null argument");
+    std::lock_guard<std::mutex> lock(mc->m);
+    out->launches = mc->launches;
+    out->max_solves = mc->max_members;
+    out->mean_solves = mc->launches ? (double)mc->members / mc->launches : 0.0;
+    return VIE_OK;
+}
+
+namespace vie {
+// A solve inside a session: it takes part in the merged launches from its first preconditioner
+// application on when its grid has blocks that fit the persistent solver (joined = already counted).
+static int solve_member(vie_merge_session* mc, vie_grid* g, const vie_spectrum* sp, const void* einc, void* e,
+                        const vie_solve_opts* o, cudaStream_t s, vie_solve_stats* stats, bool joined) {
+    MergeMember mm;
+    mm.ctx = mc;
+    mm.live = joined;
+    if (!joined && o && o->use_precond && g) {
+        const int pi = o->mode == VIE_MODE_MIXED ? 1 : 0;
+        bool fit = false;
+        for (const Group& gr : g->groups) fit = fit || gr.fit[pi];
+        if (fit) merge_join(&mm);
+    }
+    const int rc = solve_impl(g, sp, einc, e, o, s, stats, &mm);
+    merge_leave(&mm);
+    return rc;
+}
+
+static bool member_fits(const vie_grid* g, const vie_solve_opts* o) {
+    if (!g || !o || !o->use_precond) return false;
+    const int pi = o->mode == VIE_MODE_MIXED ? 1 : 0;
+    for (const Group& gr : g->groups)
+        if (gr.fit[pi]) return true;
+    return false;
+}
+}  // namespace vie
+
+extern "C" int vie_solve_merged(vie_merge_session* mc, vie_grid* g, const vie_spectrum* sp, const void* einc, void* e,
+                                const vie_solve_opts* o, vie_stream_t stream, vie_solve_stats* stats) {
+    if (!mc) return fail(VIE_EINVAL, "vie_solve_merged: null session");
+    {
+        std::lock_guard<std::mutex> lock(mc->m);
+        mc->inside++;
+    }
+    const int rc = solve_member(mc, g, sp, einc, e, o, (cudaStream_t)stream, stats, false);
+    std::lock_guard<std::mutex> lock(mc->m);
+    mc->inside--;
+    return rc;
+}
+
+// Several solves at once in a session of their own: one host thread and one stream per solve,
+// all of them members from the start (so the first applications already merge).
+extern "C" int vie_solve_many(int32_t n, vie_grid* const* grids, const vie_spectrum* const* spectra,
+                              const void* const* einc_dev, void* const* e_dev, const vie_solve_opts* opts,
+                              vie_stream_t stream, vie_solve_stats* stats, vie_merge_stats* merge) {
+    if (n < 1 || !grids || !spectra || !einc_dev || !e_dev || !opts)
+        return fail(VIE_EINVAL, "vie_solve_many: null argument or n < 1");
+    if (merge) memset(merge, 0, sizeof(*merge));
+    for (int i = 0; i < n; ++i) {
+        if (!grids[i]) return fail(VIE_EINVAL, "vie_solve_many: null grid");
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == grids[i]) return fail(VIE_EINVAL, "vie_solve_many: a grid appears twice");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 1) return solve_impl(grids[0], spectra[0], einc_dev[0], e_dev[0], &opts[0], s, stats, nullptr);
+    vie_merge_session* mc = nullptr;
+    VIE_TRY(vie_merge_session_create(&mc));
+    std::vector<cudaStream_t> st(n, nullptr);
+    cudaEvent_t start = nullptr;
+    cudaError_t ce = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventRecord(start, s);
+    for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+        ce = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st[i], start, 0);
+    }
+    auto cleanup = [&]() {
+        for (auto x : st)
+            if (x) cudaStreamDestroy(x);
+        if (start) cudaEventDestroy(start);
+        vie_merge_session_destroy(mc);
+    };
+    if (ce != cudaSuccess) {
+        const int rc = cuda_fail(ce, "vie_solve_many: stream set-up", __FILE__, __LINE__);
+        cleanup();
+        return rc;
+    }
+    std::vector<char> joined(n, 0);
+    for (int i = 0; i < n; ++i)
+        if (member_fits(grids[i], &opts[i])) {
+            joined[i] = 1;
+            mc->live++;
+        }
+    std::vector<int> rcs(n, VIE_OK);
+    std::vector<std::string> errs(n);
+    std::vector<vie_solve_stats> local(n);
+    auto run = [&](int i) {
+        memset(&local[i], 0, sizeof(vie_solve_stats));
+        cudaError_t e = cudaSetDevice(grids[i]->device);
+        int r = e == cudaSuccess
+                    ? solve_member(mc, grids[i], spectra[i], einc_dev[i], e_dev[i], &opts[i], st[i], &local[i], joined[i])
+                    : cuda_fail(e, "cudaSetDevice", __FILE__, __LINE__);
+        if (r != VIE_OK) errs[i] = g_last_error;
+        local[i].status = r;
+        rcs[i] = r;
+    };
+    {
+        std::vector<std::thread> th;
+        th.reserve(n);
+        for (int i = 0; i < n; ++i) th.emplace_back(run, i);
+        for (auto& t : th) t.join();
+    }
+    if (stats)
+        for (int i = 0; i < n; ++i) stats[i] = local[i];
+    if (merge) vie_merge_session_stats(mc, merge);
+    // the caller's stream continues after every solve's work
+    for (int i = 0; i < n; ++i) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, st[i]);
+            cudaStreamWaitEvent(s, ev, 0);
+            cudaEventDestroy(ev);
+        }
+    }
+    cleanup();
+    for (int i = 0; i < n; ++i)
+        if (rcs[i] != VIE_OK) {
+            set_error("vie_solve_many: solve " + std::to_string(i) + ": " + errs[i]);
+            return rcs[i];
+        }
+    return VIE_OK;
 }

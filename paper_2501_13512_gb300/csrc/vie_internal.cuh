@@ -169,6 +169,8 @@ constexpr int kMaxCtaPerSeg = 256;
 struct Group {
     bool persistent128 = false;        // solved by the persistent block solver
     bool persistent64 = false;
+    bool fit[2] = {false, false};      // may join a merged persistent launch (0: complex128, 1: complex64)
+    std::vector<float> last_iters[2];  // inner iterations of each block in its last application
     BoxSet bs;
     KrylovVecs<double2> k128;
     KrylovVecs<float2> k64;

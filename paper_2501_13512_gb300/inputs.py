@@ -24,7 +24,10 @@ Workloads (synthetic stand-ins for the paper's studies, Section III):
                  eps_r -15 - 1j, radius ~ U[6, 12] voxels; one block per sphere
                  plus the slab split in x into 4 blocks (Section III.B);
   * blob:        cubic grid with a smoothed random level-set blob,
-                 eps_r ~ U[2, 8], random incidence (batched instances).
+                 eps_r ~ U[2, 8], random incidence (batched instances);
+  * serving_draws: a stream of solve requests on n^3 grids (n from a size mix),
+                 metasurface tiles and solar-cell slabs rescaled to n, h = 10 nm,
+                 wavelengths on a 10 nm grid, tilted plane waves.
 """
 from __future__ import annotations
 
@@ -241,3 +244,55 @@ WORKLOADS = {
     "solar_cell": solar_cell,
     "blob": blob,
 }
+
+
+SERVING_SIZES = (32, 64, 96, 128)
+SERVING_SIZE_WEIGHTS = (0.4, 0.3, 0.2, 0.1)
+SERVING_WAVELENGTHS_NM = tuple(range(400, 801, 10))
+
+
+def serving_geometry(kind, n, sid):
+    """The structure `kind` on an n^3 grid (n >= 32), seed sid:
+    * 'metasurface': (n/16)^2 unit cells of the metasurface workload (period 16 voxels, pillars
+      16 voxels tall, eps_r 6.25, one block per pillar), centred in z in an n^3 box of air;
+    * 'solar_cell': the solar-cell workload's recipe on an n x n x n grid: metal spheres (eps_r
+      -15 - 1j) on a lattice of min(32, n) voxels, radius U[6, 12] voxels within the slab, in an
+      absorber slab (eps_r 3 - 0.3j) 40 voxels thick centred in z (n >= 48; for n = 32 the layers
+      [6, 26)), one block per sphere and the slab in 4 blocks along x."""
+    if kind == "metasurface":
+        cells = n // 16
+        tile = metasurface(cells=cells, period=16, nz=16, seed=sid)
+        z0 = (n - 16) // 2
+        eps_r = np.ones((n, n, n), np.complex128)
+        bid = np.full((n, n, n), -1, np.int32)
+        eps_r[z0:z0 + 16] = tile.eps_r
+        bid[z0:z0 + 16] = tile.block_id
+        return Workload("metasurface", (n, n, n), tile.h, tile.lambda0, eps_r, bid, inner_tol=1e-2,
+                        outer_tol=1e-6, use_precond=True)
+    if kind == "solar_cell":
+        z0, z1 = ((n - 40) // 2, (n - 40) // 2 + 40) if n >= 48 else (n // 5, n // 5 + (5 * n) // 8)
+        return solar_cell(nx=n, ny=n, nz=n, seed=sid, slab=(z0, z1), lattice=min(32, n), rmin=6,
+                          rmax=min(12, (z1 - z0) // 2 - 1))
+    raise ValueError(f"unknown structure kind {kind!r}")
+
+
+def serving_draws(nreq, seed=0, sizes=SERVING_SIZES, weights=SERVING_SIZE_WEIGHTS, structures_per_size=2,
+                  kinds=("metasurface", "solar_cell")):
+    """Parameters of a seeded stream of solve requests: request i has structure kind kinds[i % len(kinds)],
+    a grid size n drawn from `sizes` with probabilities `weights`, one of `structures_per_size` seeded
+    geometries of that kind and size, a wavelength from the 10 nm grid 400..800 nm and an incidence angle
+    U[0, pi/6] in the xz plane (polarisation in the plane of incidence, perpendicular to khat).
+    Returns dicts with keys kind, n, sid, structure (a cache key), lambda_nm, khat, pol."""
+    rng = np.random.default_rng(seed)
+    out = []
+    p = np.asarray(weights, float) / np.sum(weights)
+    for i in range(nreq):
+        n = int(rng.choice(sizes, p=p))
+        kind = kinds[i % len(kinds)]
+        sid = int(rng.integers(structures_per_size))
+        lam = float(rng.choice(SERVING_WAVELENGTHS_NM))
+        th = rng.uniform(0, np.pi / 6)
+        out.append({"kind": kind, "n": n, "sid": sid, "structure": f"{kind}-{n}-{sid}", "lambda_nm": lam,
+                    "khat": np.array([np.sin(th), 0.0, np.cos(th)]),
+                    "pol": np.array([np.cos(th), 0.0, -np.sin(th)], complex)})
+    return out

@@ -121,9 +121,14 @@ class GridEntry:
 class GpuEngine:
     """Device side: grid pool per structure, spectrum cache, one stream per worker."""
 
-    def __init__(self, max_spectra: int = 64, cache_bytes: int = 32 << 30):
+    def __init__(self, max_spectra: int = 64, cache_bytes: int = 32 << 30, merge: bool = False):
         from . import vie  # noqa: F401  (fails loudly without the CUDA library)
         self.vie = vie
+        # merge: concurrent solves of grids of the same size share persistent block-solver launches
+        # (continuous batching of the preconditioner's block solves across requests); one session per
+        # grid size keeps the solves that wait for one another in lockstep of similar cost
+        self.merge = merge
+        self.sessions: dict = {}
         self.cache_bytes = cache_bytes
         self.lock = threading.Lock()
         self.grids: dict = collections.defaultdict(list)   # structure -> [GridEntry]
@@ -193,7 +198,8 @@ class GpuEngine:
                 skey, sp = self._spectrum(req.structure, g, req.k0)
                 einc = g.plane_wave(req.k0, req.khat, req.pol)
                 e, st = g.solve(sp, einc, outer_tol=req.outer_tol, inner_tol=req.inner_tol,
-                                use_precond=req.use_precond, mode=req.mode, outer_maxit=req.outer_maxit)
+                                use_precond=req.use_precond, mode=req.mode, outer_maxit=req.outer_maxit,
+                                session=self._session(req))
                 field = e.cpu().numpy() if req.want_field else None
                 stream.synchronize()
             finally:
@@ -204,6 +210,33 @@ class GpuEngine:
                     entry.last_used = time.perf_counter()
                 self._trim()
         return Result(field, st, 0.0, 0.0)
+
+    def _session(self, req):
+        if not self.merge:
+            return None
+        key = tuple(req.eps_r.shape)
+        with self.lock:
+            if key not in self.sessions:
+                self.sessions[key] = self.vie.MergeSession()
+            return self.sessions[key]
+
+    def merge_stats(self):
+        """Merged launches summed over the sessions (None without merging)."""
+        if not self.merge:
+            return None
+        tot = {"launches": 0, "max_solves": 0, "solve_slots": 0.0}
+        for s in self.sessions.values():
+            st = s.stats()
+            tot["launches"] += st["launches"]
+            tot["max_solves"] = max(tot["max_solves"], st["max_solves"])
+            tot["solve_slots"] += st["launches"] * st["mean_solves"]
+        tot["mean_solves"] = tot.pop("solve_slots") / tot["launches"] if tot["launches"] else 0.0
+        return tot
+
+    def close(self):
+        for s in self.sessions.values():
+            s.close()
+        self.sessions = {}
 
     def _trim(self):
         """Destroy least recently used idle grids (and their spectra) beyond cache_bytes."""
@@ -227,9 +260,9 @@ class GpuEngine:
 class Server:
     """submit() returns a Future of Result; solves overlap on `slots` streams."""
 
-    def __init__(self, budget_bytes: int, slots: int = 4, engine=None, max_bypass: int = 8):
+    def __init__(self, budget_bytes: int, slots: int = 4, engine=None, max_bypass: int = 8, merge: bool = False):
         self.sched = Scheduler(budget_bytes, slots, max_bypass)
-        self.engine = engine if engine is not None else GpuEngine()
+        self.engine = engine if engine is not None else GpuEngine(merge=merge)
         self.cv = threading.Condition()
         self.stop = False
         self.done: list = []
@@ -287,6 +320,8 @@ class Server:
             self.cv.notify_all()
         for t in self.workers:
             t.join(timeout=timeout)
+        if hasattr(self.engine, "close") and not any(t.is_alive() for t in self.workers):
+            self.engine.close()
 
     def latency_stats(self):
         lat = np.array([r.t_done - r.t_submit for r in self.done if r.t_done > 0])
@@ -294,43 +329,35 @@ class Server:
             return {}
         t0 = min(r.t_submit for r in self.done)
         t1 = max(r.t_done for r in self.done)
+        by_size = {}
+        for r in self.done:
+            if r.t_done > 0:
+                by_size.setdefault(int(round(r.nvox ** (1 / 3))), []).append(r.t_done - r.t_submit)
         return {"requests": int(lat.size), "p50_s": float(np.percentile(lat, 50)),
-                "p99_s": float(np.percentile(lat, 99)), "solves_per_s": lat.size / max(1e-9, t1 - t0)}
+                "p99_s": float(np.percentile(lat, 99)), "solves_per_s": lat.size / max(1e-9, t1 - t0),
+                "p50_s_by_size": {n: float(np.percentile(v, 50)) for n, v in sorted(by_size.items())}}
 
 
 # ---------------------------------------------------------------- synthetic request stream
-SIZES = (32, 64, 96, 128)
-SIZE_WEIGHTS = (0.4, 0.3, 0.2, 0.1)
-WAVELENGTHS_NM = tuple(range(400, 801, 10))
+from .inputs import SERVING_SIZE_WEIGHTS as SIZE_WEIGHTS, SERVING_SIZES as SIZES  # noqa: E402
 
 
 def make_stream(nreq, seed=0, sizes=SIZES, weights=SIZE_WEIGHTS, h_nm=10.0, structures_per_size=2,
-                kinds=("metasurface", "solar_cell"), outer_maxit=1000):
-    """Serving workload: grids drawn from `sizes`, structures alternating metasurface
-    tiles and particle slabs rescaled to n, wavelength from a 10 nm sweep grid,
-    random incidence angle (x-polarised plane waves tilted in the xz plane)."""
+                kinds=("metasurface", "solar_cell"), outer_maxit=1000, mode=1):
+    """Serving workload (inputs.serving_draws): grids drawn from `sizes`, structures
+    alternating metasurface tiles and particle slabs rescaled to n, wavelength from a
+    10 nm sweep grid, random incidence angle (plane waves tilted in the xz plane).
+    `mode` is the solve mode of every request (1 mixed, 0 complex128 throughout,
+    both with the block preconditioner); the draws do not depend on it, so two
+    streams with the same seed hold the same problems."""
     from . import inputs
-    rng = np.random.default_rng(seed)
     geo = {}
     out = []
-    for i in range(nreq):
-        n = int(rng.choice(sizes, p=np.asarray(weights) / np.sum(weights)))
-        kind = kinds[i % len(kinds)]
-        sid = int(rng.integers(structures_per_size))
-        key = f"{kind}-{n}-{sid}"
+    for d in inputs.serving_draws(nreq, seed, sizes, weights, structures_per_size, kinds):
+        key = d["structure"]
         if key not in geo:
-            if kind == "metasurface":
-                cells = max(1, n // 16)
-                w = inputs.metasurface(cells=cells, period=n // cells, nz=n, seed=sid)
-            else:
-                w = inputs.solar_cell(nx=n, ny=n, nz=n, seed=sid, slab=(n // 5, n // 5 + (5 * n) // 8),
-                                      lattice=n // 2, rmin=max(2, n // 20), rmax=max(3, n // 11))
-            geo[key] = w
+            geo[key] = inputs.serving_geometry(d["kind"], d["n"], d["sid"])
         w = geo[key]
-        lam = float(rng.choice(WAVELENGTHS_NM))
-        th = rng.uniform(0, np.pi / 6)
-        khat = np.array([np.sin(th), 0.0, np.cos(th)])
-        pol = np.array([np.cos(th), 0.0, -np.sin(th)], complex)
-        out.append(Request(structure=key, eps_r=w.eps_r, h=h_nm, k0=2 * np.pi / lam, khat=khat, pol=pol,
-                           block_id=w.block_id, outer_maxit=outer_maxit))
+        out.append(Request(structure=key, eps_r=w.eps_r, h=h_nm, k0=2 * np.pi / d["lambda_nm"], khat=d["khat"],
+                           pol=d["pol"], block_id=w.block_id, outer_maxit=outer_maxit, mode=mode))
     return out

@@ -61,6 +61,10 @@ class SolveStats(ctypes.Structure):
                 ("elapsed_ms", c_double)]
 
 
+class MergeStats(ctypes.Structure):
+    _fields_ = [("launches", c_int32), ("max_solves", c_int32), ("mean_solves", c_double)]
+
+
 class BatchDesc(ctypes.Structure):
     _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("h", c_double), ("count", c_int32),
                 ("eps_r", POINTER(c_double)), ("flags", c_uint32)]
@@ -106,6 +110,12 @@ def load(path=LIB_PATH):
         "vie_matvec": ([P, P, c_int, P, P, P], c_int),
         "vie_block_precond_apply": ([P, P, c_int, P, P, c_double, c_int, P, POINTER(PrecondStats)], c_int),
         "vie_solve": ([P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
+        "vie_merge_session_create": ([POINTER(P)], c_int),
+        "vie_merge_session_destroy": ([P], c_int),
+        "vie_merge_session_stats": ([P, POINTER(MergeStats)], c_int),
+        "vie_solve_merged": ([P, P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
+        "vie_solve_many": ([c_int32, POINTER(P), POINTER(P), POINTER(P), POINTER(P), POINTER(SolveOpts), P,
+                            POINTER(SolveStats), POINTER(MergeStats)], c_int),
         "vie_matvec_noalloc": ([c_int32, c_int32, c_int32, c_double, c_double, P, P, P, P], c_int),
         "vie_far_field_rcs": ([P, c_double, P, c_int32, POINTER(c_double), POINTER(c_double), P], c_int),
         "vie_batch_create": ([POINTER(BatchDesc), POINTER(P)], c_int),
@@ -301,16 +311,27 @@ class Grid:
                                               _stream(), byref(st)))
         return y, _struct_dict(st)
 
+    def _opts(self, outer_tol=1e-6, inner_tol=1e-2, outer_maxit=1000, inner_maxit=1000, use_precond=True,
+              mode=MODE_MIXED, max_refinements=0, wait_timeout_ms=0.0, x0=None):
+        return SolveOpts(float(outer_tol), float(inner_tol), int(outer_maxit), int(inner_maxit), int(bool(use_precond)),
+                         int(mode), int(max_refinements), float(wait_timeout_ms),
+                         None if x0 is None else self._vec(x0, C128, "x0"))
+
     def solve(self, spec, einc, e=None, outer_tol=1e-6, inner_tol=1e-2, outer_maxit=1000, inner_maxit=1000,
-              use_precond=True, mode=MODE_MIXED, max_refinements=0, wait_timeout_ms=0.0, x0=None, check=True):
-        """x0: initial guess (complex128 CUDA tensor, may be `e` itself), None for zero."""
+              use_precond=True, mode=MODE_MIXED, max_refinements=0, wait_timeout_ms=0.0, x0=None, check=True,
+              session=None):
+        """x0: initial guess (complex128 CUDA tensor, may be `e` itself), None for zero.
+        session: a MergeSession whose concurrent solves share block-solver launches (vie_solve_merged)."""
         e = self.empty(C128) if e is None else e
-        o = SolveOpts(float(outer_tol), float(inner_tol), int(outer_maxit), int(inner_maxit), int(bool(use_precond)),
-                      int(mode), int(max_refinements), float(wait_timeout_ms),
-                      None if x0 is None else self._vec(x0, C128, "x0"))
+        o = self._opts(outer_tol, inner_tol, outer_maxit, inner_maxit, use_precond, mode, max_refinements,
+                       wait_timeout_ms, x0)
         st = SolveStats()
-        rc = load().vie_solve(self.handle, spec.handle, self._vec(einc, C128, "einc"), self._vec(e, C128, "e"),
-                              byref(o), _stream(), byref(st))
+        args = (self.handle, spec.handle, self._vec(einc, C128, "einc"), self._vec(e, C128, "e"), byref(o),
+                _stream(), byref(st))
+        if session is None:
+            rc = load().vie_solve(*args)
+        else:
+            rc = load().vie_solve_merged(session.handle, *args)
         if check:
             _check(rc, allow=(VIE_ENOTCONV,))
         return e, _struct_dict(st)
@@ -333,6 +354,61 @@ class Grid:
         out_host.copy_(e, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return out_host, st
+
+
+class MergeSession:
+    """Solves run concurrently (own threads and streams) inside a session share persistent block-solver
+    launches (vie_merge_session_*)."""
+
+    def __init__(self):
+        h = c_void_p()
+        _check(load().vie_merge_session_create(byref(h)))
+        self.handle = h
+
+    def stats(self):
+        ms = MergeStats()
+        _check(load().vie_merge_session_stats(self.handle, byref(ms)))
+        return _struct_dict(ms)
+
+    def close(self):
+        if self.handle:
+            _check(load().vie_merge_session_destroy(self.handle))
+            self.handle = None
+
+
+def _addr(p):
+    return p.value if isinstance(p, c_void_p) else p
+
+
+def solve_many(problems, check=True):
+    """Solves several systems at once (vie_solve_many): each problem is a dict with keys grid, spec, einc,
+    optionally e, and any option of Grid.solve (outer_tol, inner_tol, mode, ...); the grids must be distinct.
+    Block-preconditioner applications of all solves share persistent launches. Returns
+    ([(e, stats) per problem], merge stats)."""
+    n = len(problems)
+    grids = (c_void_p * n)()
+    specs = (c_void_p * n)()
+    ein = (c_void_p * n)()
+    eout = (c_void_p * n)()
+    opts = (SolveOpts * n)()
+    stats = (SolveStats * n)()
+    fields = []
+    for i, p in enumerate(problems):
+        g = p["grid"]
+        e = p.get("e")
+        e = g.empty(C128) if e is None else e
+        fields.append(e)
+        kw = {k: v for k, v in p.items() if k not in ("grid", "spec", "einc", "e")}
+        grids[i] = _addr(g.handle)
+        specs[i] = _addr(p["spec"].handle)
+        ein[i] = _addr(g._vec(p["einc"], C128, "einc"))
+        eout[i] = _addr(g._vec(e, C128, "e"))
+        opts[i] = g._opts(**kw)
+    ms = MergeStats()
+    rc = load().vie_solve_many(n, grids, specs, ein, eout, opts, _stream(), stats, byref(ms))
+    if check:
+        _check(rc, allow=(VIE_ENOTCONV,))
+    return [(fields[i], _struct_dict(stats[i])) for i in range(n)], _struct_dict(ms)
 
 
 class Rooftop:
