@@ -681,6 +681,11 @@ constexpr int kSlabThreads = VIE_SLAB_THREADS;
 #ifndef VIE_SLAB_INLINE
 #define VIE_SLAB_INLINE __noinline__
 #endif
+// CTAs per SM the slab kernel's register budget leaves room for (2 caps it at 128 registers)
+#ifndef VIE_SLAB_MINB
+#define VIE_SLAB_MINB 1
+#endif
+constexpr int kSlabMinBlocks = VIE_SLAB_MINB;
 #ifndef VIE_SLAB_BATCH
 #define VIE_SLAB_BATCH 4
 #endif
@@ -1301,10 +1306,11 @@ __device__ __forceinline__ void solve_dispatch(const InnerGroup<float2>& g, int 
     }
 }
 
-// SLAB: the kernel of launches whose complex64 groups use the slab MVM (512 threads, one CTA per
-// SM); otherwise 256 threads and two CTAs per SM. npl: kz planes per round of the slab plane stage.
+// SLAB: the kernel of launches whose complex64 groups use the slab MVM (kSlabThreads threads,
+// kSlabMinBlocks CTAs per SM at least); otherwise 256 threads and two CTAs per SM. npl: kz planes per
+// round of the slab plane stage.
 template <class C, bool SLAB>
-__global__ void __launch_bounds__(SLAB ? kSlabThreads : kInnerThreads, SLAB ? 1 : 2)
+__global__ void __launch_bounds__(SLAB ? kSlabThreads : kInnerThreads, SLAB ? kSlabMinBlocks : 2)
     k_inner(const InnerGroup<C>* groups, const int2* work, int nwork, int* next, double tol, int maxit, const C* tw,
             int* units, int npl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1351,6 +1357,16 @@ int inner_cluster_forced() {
         const char* e = getenv("VIE_INNER_CLUSTER");
         int v = e ? atoi(e) : 0;
         return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
+    }();
+    return r;
+}
+
+// VIE_SLAB_NPL = 2 or 4: kz planes per round of the slab plane stage (default: 4 where it fits)
+static int slab_npl_forced() {
+    static const int r = [] {
+        const char* e = getenv("VIE_SLAB_NPL");
+        const int v = e ? atoi(e) : 0;
+        return (v == 2 || v == 4) ? v : 0;
     }();
     return r;
 }
@@ -1495,9 +1511,9 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
     // dynamic shared memory and planes per round of a launch with R CTAs per block
     auto launch_smem = [&](int R, int* npl) -> size_t {
         size_t m = smem;
-        *npl = 4;
+        *npl = slab_npl_forced() ? slab_npl_forced() : 4;
         for (const BoxSet* b : slab_sets)
-            if (slab_smem(*b, R, 4) > kSlabSmemLimit) *npl = 2;
+            if (slab_smem(*b, R, *npl) > kSlabSmemLimit) *npl = 2;
         for (const BoxSet* b : slab_sets) m = std::max(m, slab_smem(*b, R, *npl));
         return m;
     };
