@@ -974,11 +974,6 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             batched.push_back(i);
         }
     }
-    // cluster size: two candidates for every block, then the split launch (the slowest blocks of the
-    // previous apply on the larger cluster, the rest on the smaller one), tried on the first three
-    // applies; then the best. Register-FFT MVM: 2, 4, split 4/2. Slab MVM (whole MVM on chip, the
-    // cluster splits the kz planes): 2, 1, 4 (a split cannot shorten the slowest block's solve, which
-    // bounds the apply once every block fits on the device at once).
     // after arriving, the request is waited for on every path out of this function
     if (merged && !any_fit) merge_leave(mm);   // nothing of this grid fits: do not hold the others
     MergeReq req;
@@ -1004,12 +999,24 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     }
     bool slab = false;
     for (const InnerJob<C>& j : jobs) slab = slab || j.Go != nullptr;
-    static const int kCand[3] = {2, 4, -1};
-    static const int kCandSlab[3] = {2, 1, 4};
+    // launch shape, tuned on the first applies, then the best. Register-FFT MVM: 2 and 4 CTAs per
+    // block, then the split launch (the slowest blocks of the previous apply on 4 CTAs, the rest on 2).
+    // Slab MVM (whole MVM on chip, the cluster splits the kz planes): 2, 1 and 4 CTAs with 4 planes per
+    // round where they fit, then 2 CTAs with 2 planes per round (a split cannot shorten the slowest
+    // block's solve, which bounds the apply once every block fits on the device at once).
+    // candidates (CTAs per block, kz planes per round of the slab MVM's plane stage; 0 = as many as fit)
+    struct Cand {
+        int cluster, npl;
+    };
+    static const Cand kCand[3] = {{2, 0}, {4, 0}, {-1, 0}};
+    static const Cand kCandSlab[4] = {{2, 4}, {1, 4}, {4, 4}, {2, 2}};
+    const int ncand = slab ? 4 : 3;
     const int pi = c128 ? 0 : 1;
     const int tried = g->tune_count[pi];
-    const bool tuning = !jobs.empty() && tried < 3 && !inner_cluster_forced();
-    const int choice = tuning ? (slab ? kCandSlab : kCand)[tried] : (g->tune_best[pi] ? g->tune_best[pi] : 2);
+    const bool tuning = !jobs.empty() && tried < ncand && !inner_cluster_forced();
+    const Cand cand = tuning ? (slab ? kCandSlab : kCand)[tried]
+                             : Cand{g->tune_best[pi] ? g->tune_best[pi] : 2, g->tune_npl[pi]};
+    const int choice = cand.cluster;
     // with batched groups as well, the persistent launch runs on the grid's second stream beside
     // the batched steps (no split launch then)
     const bool beside = !jobs.empty() && !batched.empty();
@@ -1028,7 +1035,7 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     if (tuning) VIE_CK(cudaEventRecord(g->tev[0], sp_stream));
     VIE_TRY(inner_persistent<C>(jobs, c128 ? g->work128 : g->work64, c128 ? g->nwork128 : g->nwork64,
                                 g->inner_groups, g->inner_next, tol, maxit, sp_stream,
-                                choice == -1 ? (slab ? 1 : 2) : choice, &split));
+                                choice == -1 ? (slab ? 1 : 2) : choice, &split, cand.npl));
     if (tuning) VIE_CK(cudaEventRecord(g->tev[1], sp_stream));
     std::vector<Bicg<C>> bk(ng);
     for (int i : batched) {
@@ -1134,19 +1141,24 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
         VIE_TRY(wait_event(g->tev[1], timeout_ms));
         float ms = 0.f;
         VIE_CK(cudaEventElapsedTime(&ms, g->tev[0], g->tev[1]));
-        int maxit_seen = 1;
+        // the applies differ in their blocks' iteration counts: score the launch time per unit of
+        // block work (iterations x padded box of every persistent block), since with every block
+        // queued the launch drains the whole queue at the rate its clusters sustain
+        double work = 0.0;
         std::vector<SegState> hs;
         for (auto& gr : g->groups) {
+            if (!(c128 ? gr.persistent128 : gr.persistent64)) continue;
             hs.resize(gr.bs.nb);
             VIE_CK(cudaMemcpy(hs.data(), gr.st, gr.bs.nb * sizeof(SegState), cudaMemcpyDeviceToHost));
-            for (auto& st : hs) maxit_seen = std::max(maxit_seen, (int)std::ceil(st.iters));
+            for (auto& st : hs) work += (st.iters + 1.0) * (double)gr.bs.spec_elems();
         }
-        g->tune_score[pi][tried] = ms / maxit_seen;
-        if (++g->tune_count[pi] == 3) {
+        g->tune_score[pi][tried] = ms / std::max(work, 1.0);
+        if (++g->tune_count[pi] == ncand) {
             int best = 0;
-            for (int k = 1; k < 3; ++k)
+            for (int k = 1; k < ncand; ++k)
                 if (g->tune_score[pi][k] < g->tune_score[pi][best]) best = k;
-            g->tune_best[pi] = (slab ? kCandSlab : kCand)[best];
+            g->tune_best[pi] = (slab ? kCandSlab : kCand)[best].cluster;
+            g->tune_npl[pi] = (slab ? kCandSlab : kCand)[best].npl;
         }
     }
     return VIE_OK;

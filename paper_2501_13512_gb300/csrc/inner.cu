@@ -1445,7 +1445,8 @@ bool inner_persistent_ok(const BoxSet& bs, size_t es, bool force) {
 
 template <class C>
 int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, int nwork, void* d_groups,
-                     int* d_next, double tol, int maxit, cudaStream_t s, int cluster, const InnerSplit* split) {
+                     int* d_next, double tol, int maxit, cudaStream_t s, int cluster, const InnerSplit* split,
+                     int npl_pref) {
     if (jobs.empty() || nwork == 0) return VIE_OK;
     Twiddles tw;
     VIE_TRY(get_twiddles(&tw));
@@ -1511,7 +1512,7 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
     // dynamic shared memory and planes per round of a launch with R CTAs per block
     auto launch_smem = [&](int R, int* npl) -> size_t {
         size_t m = smem;
-        *npl = slab_npl_forced() ? slab_npl_forced() : 4;
+        *npl = slab_npl_forced() ? slab_npl_forced() : (npl_pref == 2 ? 2 : 4);
         for (const BoxSet* b : slab_sets)
             if (slab_smem(*b, R, *npl) > kSlabSmemLimit) *npl = 2;
         for (const BoxSet* b : slab_sets) m = std::max(m, slab_smem(*b, R, *npl));
@@ -1571,9 +1572,9 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
 }
 
 template int inner_persistent<double2>(const std::vector<InnerJob<double2>>&, const int2*, int, void*, int*, double,
-                                       int, cudaStream_t, int, const InnerSplit*);
+                                       int, cudaStream_t, int, const InnerSplit*, int);
 template int inner_persistent<float2>(const std::vector<InnerJob<float2>>&, const int2*, int, void*, int*, double, int,
-                                      cudaStream_t, int, const InnerSplit*);
+                                      cudaStream_t, int, const InnerSplit*, int);
 
 __global__ void k_slab_spectrum(const double2* __restrict__ G, float2* __restrict__ Go, int Mx, int My, int Mz, int lx,
                                 int ly, int lz) {

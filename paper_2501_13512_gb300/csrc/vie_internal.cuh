@@ -235,7 +235,8 @@ struct vie_grid {
     // applies 0 and 1 try the candidates, later applies use the best
     int tune_count[2] = {0, 0};
     int tune_best[2] = {0, 0};
-    double tune_score[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int tune_npl[2] = {0, 0};             // slab MVM: kz planes per round of the best candidate (0: auto)
+    double tune_score[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     int nheavy[2] = {0, 0};               // blocks of the split launch's heavy part (from the last apply)
     cudaEvent_t tev[2] = {nullptr, nullptr};
     int64_t device_bytes = 0;
@@ -343,7 +344,8 @@ bool slab_path_ok(const BoxSet& bs, size_t es);
 // Go[kz][c][ky][kx] = G[c][brev(kz)][brev(ky)][brev(kx)] for k in [0, M/2] per axis, as complex64.
 int slab_spectrum(const BoxSet& bs, const double2* G, float2* Go, cudaStream_t s);
 size_t inner_group_desc_bytes();
-// cluster: CTAs per block (1, 2, 4, 8; 0 = 2), unless VIE_INNER_CLUSTER forces one.
+// cluster: CTAs per block (1, 2, 4, 8; 0 = 2), unless VIE_INNER_CLUSTER forces one. npl: kz planes
+// per round of the slab MVM's plane stage (2 or 4; 0: 4 where it fits), unless VIE_SLAB_NPL forces one.
 // Split launch (split != null, 0 < split->nheavy < nwork): the first nheavy work items run
 // with split->cluster CTAs per block on s while the rest run with `cluster` CTAs per block on
 // split->s2, concurrently; d_next must hold two counters; s waits for both.
@@ -356,7 +358,7 @@ struct InnerSplit {
 template <class C>
 int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, int nwork, void* d_groups,
                      int* d_next, double tol, int maxit, cudaStream_t s, int cluster = 0,
-                     const InnerSplit* split = nullptr);
+                     const InnerSplit* split = nullptr, int npl = 0);
 int inner_cluster_forced();
 // True when the environment variable VIE_INNER_SLAB is 0: complex64 blocks keep the register-FFT MVM
 // instead of the slab MVM (read once).
