@@ -1012,9 +1012,11 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     static const Cand kCandSlab[4] = {{2, 4}, {1, 4}, {4, 4}, {2, 2}};
     const int ncand = slab ? 4 : 3;
     const int pi = c128 ? 0 : 1;
-    const int tried = g->tune_count[pi];
+    // the first apply only warms up (first launches of the kernel pay one-time costs that would bias
+    // the candidate tried first); the candidates follow, one per apply
+    const int tried = g->tune_count[pi] - 1;
     const bool tuning = !jobs.empty() && tried < ncand && !inner_cluster_forced();
-    const Cand cand = tuning ? (slab ? kCandSlab : kCand)[tried]
+    const Cand cand = tuning ? (slab ? kCandSlab : kCand)[std::max(tried, 0)]
                              : Cand{g->tune_best[pi] ? g->tune_best[pi] : 2, g->tune_npl[pi]};
     const int choice = cand.cluster;
     // with batched groups as well, the persistent launch runs on the grid's second stream beside
@@ -1137,7 +1139,6 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
         }
     }
     if (tuning) {
-        // score: persistent-launch time per iteration of its slowest block (the critical path)
         VIE_TRY(wait_event(g->tev[1], timeout_ms));
         float ms = 0.f;
         VIE_CK(cudaEventElapsedTime(&ms, g->tev[0], g->tev[1]));
@@ -1152,8 +1153,8 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
             VIE_CK(cudaMemcpy(hs.data(), gr.st, gr.bs.nb * sizeof(SegState), cudaMemcpyDeviceToHost));
             for (auto& st : hs) work += (st.iters + 1.0) * (double)gr.bs.spec_elems();
         }
-        g->tune_score[pi][tried] = ms / std::max(work, 1.0);
-        if (++g->tune_count[pi] == ncand) {
+        if (tried >= 0) g->tune_score[pi][tried] = ms / std::max(work, 1.0);
+        if (++g->tune_count[pi] == ncand + 1) {
             int best = 0;
             for (int k = 1; k < ncand; ++k)
                 if (g->tune_score[pi][k] < g->tune_score[pi][best]) best = k;
