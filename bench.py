@@ -294,6 +294,33 @@ def traffic_per_launch(kernel, algorithmic_bytes_per_launch):
     return dram * algorithmic_bytes_per_launch / rec["algorithmic_bytes_same_launch"]
 
 
+def l2_traffic_per_launch(kernel, algorithmic_bytes_per_launch):
+    """L2 bytes (lts__t_bytes) per launch from the committed ncu capture of `kernel`, scaled like
+    traffic_per_launch; None if the kernel source changed since."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    if traffic_per_launch(kernel, algorithmic_bytes_per_launch) is None:
+        return None
+    rec = json.load(open(p))
+    return rec["lts_bytes"] * algorithmic_bytes_per_launch / rec["algorithmic_bytes_same_launch"]
+
+
+def l2_copy_gbs():
+    """L2-resident copy rate of this GPU: a 24 MB buffer copied into another (48 MB touched, well inside
+    the 129 MB L2) 200 times after warm-up; read + write bytes over the CUDA-event time."""
+    import torch
+    a = torch.empty(24 << 20, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(20):
+        b.copy_(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(200):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2 * a.numel() * 200 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -603,6 +630,15 @@ def main():
                 "launches": dom["launches"], "ms_per_launch": per_launch_ms,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "share_of_kernel_time": dom["total_ms"] / tot,
                 "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        # the block solver keeps its working set on chip and in L2: its L2 traffic against an L2-resident copy
+        l2b = l2_traffic_per_launch(kname, bytes_per_launch)
+        if l2b is not None:
+            l2c = l2_copy_gbs()
+            l2a = l2b / (per_launch_ms * 1e-3) / 1e9
+            roof["onchip"] = {"bound": "l2", "achieved": l2a, "peak": l2c, "unit": "GB/s", "frac": l2a / l2c,
+                              "l2_bytes_per_launch": l2b,
+                              "source": "lts__t_bytes of the committed ncu capture scaled to this launch; peak: "
+                                        "L2-resident copy (torch copy_, 24 MB) timed here"}
         kernels = {f"{k['name']}_{k['precision']}": {"launches": k["launches"], "ms": round(k["total_ms"], 3),
                                                      "GBps": round(k["bytes"] / (k["total_ms"] * 1e-3) / 1e9, 1)}
                    for k in sorted(kstats, key=lambda k: -k["total_ms"])}
