@@ -129,3 +129,46 @@ def test_solve_many_rejects_a_grid_twice_and_runs_one_as_vie_solve():
         assert st["status"] == vie.VIE_OK and _rel(e.cpu().numpy().ravel()[idx], ref) <= 1e-5
     finally:
         _close([p])
+
+
+def _tile(kind, n, sid, lam, mode, tol=1e-6):
+    w = inputs.serving_geometry(kind, n, sid)
+    d = {"lambda_nm": lam, "khat": np.array([0.3, 0.0, np.sqrt(1 - 0.09)]),
+         "pol": np.array([np.sqrt(1 - 0.09), 0.0, -0.3], complex)}
+    return _problem(w, d, mode, tol)
+
+
+def test_solve_many_reports_a_failing_solve_and_finishes_the_others():
+    probs = [_tile("metasurface", 32, 0, 500, vie.MODE_MIXED), _tile("metasurface", 32, 1, 620, vie.MODE_MIXED),
+             _tile("metasurface", 64, 0, 560, vie.MODE_MIXED)]
+    probs[1]["outer_tol"] = 0.0                 # rejected by the solve (VIE_EINVAL) before any block work
+    try:
+        res, ms = vie.solve_many(probs, check=False)
+        assert res[1][1]["status"] == vie.VIE_EINVAL
+        for i in (0, 2):
+            e, st = res[i]
+            assert st["status"] == vie.VIE_OK and st["true_rel_res"] <= 1e-6
+            p = probs[i]
+            e1, _ = p["grid"].solve(p["spec"], p["einc"], outer_tol=1e-6, mode=vie.MODE_MIXED)
+            assert _rel(e.cpu().numpy(), e1.cpu().numpy()) <= 1e-5
+        assert ms["launches"] >= 1 and ms["max_solves"] == 2
+        with pytest.raises(vie.VieError):
+            vie.solve_many(probs)                   # the first failing solve's code, raised
+    finally:
+        _close(probs)
+
+
+def test_session_with_mixed_and_fp64_solves_launches_per_precision():
+    # complex64 blocks of the mixed solves and complex128 blocks of the FP64 solve (a 96^3 tile: 36
+    # blocks, so its grid alone takes the persistent solver) merge in separate launches of one session
+    probs = [_tile("metasurface", 96, 0, 600, vie.MODE_MIXED), _tile("metasurface", 96, 1, 610, vie.MODE_MIXED),
+             _tile("metasurface", 96, 0, 630, vie.MODE_PLAIN_C128)]
+    try:
+        res, ms = vie.solve_many(probs)
+        for (e, st), p in zip(res, probs):
+            assert st["status"] == vie.VIE_OK and st["true_rel_res"] <= 1e-6
+            e1, _ = p["grid"].solve(p["spec"], p["einc"], outer_tol=1e-6, mode=p["mode"])
+            assert _rel(e.cpu().numpy(), e1.cpu().numpy()) <= 1e-5
+        assert ms["launches"] >= 2 and ms["max_solves"] >= 2
+    finally:
+        _close(probs)
