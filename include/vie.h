@@ -105,9 +105,9 @@ typedef struct {
     int64_t device_bytes;    /* device memory held by the grid handle              */
     int32_t inner_cluster[2];/* CTAs per block chosen by the block solver's tuner for
                                 complex128 [0] and complex64 [1]: 1, 2 or 4 for
-                                every block, -1 for the split launch (the slowest
-                                blocks on 4 CTAs and the rest on 2, or on 2 and 1
-                                for the on-chip complex64 MVM); 0 = not yet tuned  */
+                                every block, -1 for the split launch of the
+                                register MVM (the slowest blocks on 4 CTAs and the
+                                rest on 2); 0 = not yet tuned                      */
 } vie_grid_info;
 
 /* Creates the grid on the current CUDA device: uploads chi = eps_r - 1,
