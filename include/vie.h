@@ -336,6 +336,24 @@ int vie_batch_solve(vie_batch* batch, const double* k0s, const void* einc_dev,
                     void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
                     vie_solve_stats* stats);
 
+/* n batches of different grid shapes at once, in a merge session of their own
+ * (see vie_solve_merged): one internal host thread and stream per batch; at
+ * every refinement step the persistent correction launches of all batches that
+ * reached it run as ONE launch (one CTA cluster per instance, instances of all
+ * sizes in one work queue, largest boxes first). Batches whose corrections use
+ * batched launches (planes too large for shared memory) run beside it. Each
+ * batch's result equals its vie_batch_solve result up to rounding.
+ * batches[n]: distinct; k0s[n], einc_dev[n], e_dev[n], opts[n], stats[n] (stats
+ * may be NULL, or stats[i] NULL): as for vie_batch_solve, per batch. merge (may
+ * be NULL): the merged launches. Ordered after the work queued on `stream`
+ * before the call and before work queued on it after. Returns VIE_OK when every
+ * batch returned VIE_OK, else the code of the first batch (by index) that did
+ * not, with its message; VIE_EINVAL for n < 1, a null array or a batch listed
+ * twice (nothing runs then). */
+int vie_batch_solve_many(int32_t n, vie_batch* const* batches, const double* const* k0s,
+                         const void* const* einc_dev, void* const* e_dev, const vie_solve_opts* opts,
+                         vie_stream_t stream, vie_solve_stats* const* stats, vie_merge_stats* merge);
+
 /* ---- The paper's rooftop / pulse discretisation (Section II.A, Eqs. 5-9). ----
  * Unknown w = J / (j w eps0) (units of E; w = chi E in the continuum), expanded in rooftops (Eq. 5):
  * component a lives on the face between cell c and cell c + e_a, stored at index c of a vector

@@ -21,6 +21,7 @@ namespace vie {
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+std::string last_error_message() { return g_last_error; }
 
 int fail(int code, const std::string& msg) {
     set_error(msg);
@@ -738,62 +739,8 @@ static int mvm_full(vie_grid* g, const vie_spectrum* sp, const C* x, C* y, cudaS
 }
 
 // ---------------------------------------------------------------- merged block-solver launches
-// Solves that run at the same time, one host thread and one stream each, inside one merge
-// session (vie_solve_merged, vie_solve_many). A preconditioner application queues its gathers on
-// its own stream and arrives here; once every solve of the session that still applies a
-// preconditioner has arrived, the last one to arrive queues ONE persistent launch over the blocks
-// of all of them (one per precision, inner tolerance and iteration limit) on the session's merge
-// stream. Each solve's stream then waits for that launch before its blocks are scattered back.
-// Each block's work is the same as in a launch of its grid alone.
-struct MergeReq {
-    vie_grid* g = nullptr;
-    const vie_spectrum* sp = nullptr;
-    int prec = 0;                  // 0: complex128, 1: complex64
-    double tol = 0.0;
-    int maxit = 0;
-    cudaEvent_t ready = nullptr;   // recorded on the solve's stream after its gathers
-    int64_t gen = -1;              // launch that took it (-1: none yet, -2: that launch failed)
-};
-
-struct MergeLaunch {
-    cudaEvent_t done = nullptr;
-    int waiting = 0;               // members that have not yet made their stream wait for it
-};
-
-}  // namespace vie
-
-struct vie_merge_session {
-    std::mutex m;
-    std::condition_variable cv;
-    int device = 0;
-    int live = 0;                  // solves that may still arrive
-    int inside = 0;                // solves inside the session
-    std::vector<vie::MergeReq*> pending;
-    cudaStream_t ms = nullptr;     // every merged launch, in order
-    std::map<int64_t, vie::MergeLaunch> launches_open;
-    std::vector<cudaEvent_t> free_events;
-    int64_t next_gen = 0;
-    char* d_groups = nullptr;      // group descriptors of a launch
-    int2* d_work = nullptr;        // (job, box) work list of a launch
-    int* d_next = nullptr;
-    int64_t groups_cap = 0, work_cap = 0;
-    std::vector<void*> retired;    // outgrown buffers (a queued launch may still read them)
-    int launches = 0;
-    int64_t members = 0;
-    int max_members = 0;
-    std::string err;
-};
-
-namespace vie {
-
-using MergeCtx = vie_merge_session;
-
-// One solve's membership: it leaves (once) when it stops applying the preconditioner.
-struct MergeMember {
-    MergeCtx* ctx = nullptr;
-    bool live = false;
-};
-
+// (vie_internal.cuh describes the session.) Members build their jobs and work items and arrive;
+// the last member to arrive queues the launches on the session's stream.
 static int merge_capacity(MergeCtx* mc, int64_t ngroups, int64_t nwork) {
     if (ngroups > mc->groups_cap) {
         char* p = nullptr;
@@ -815,31 +762,23 @@ static int merge_capacity(MergeCtx* mc, int64_t ngroups, int64_t nwork) {
     return VIE_OK;
 }
 
+template <class C> static std::vector<InnerJob<C>>& req_jobs(MergeReq* r);
+template <> std::vector<InnerJob<double2>>& req_jobs<double2>(MergeReq* r) { return r->j128; }
+template <> std::vector<InnerJob<float2>>& req_jobs<float2>(MergeReq* r) { return r->j64; }
+
+// One launch over the jobs of every request (same precision, tolerance and limit), the work
+// items of all of them longest first.
 template <class C>
 static int merged_launch(MergeCtx* mc, const std::vector<MergeReq*>& reqs) {
-    const int pi = prec_of<C>() == VIE_C128 ? 0 : 1;
     std::vector<InnerJob<C>> jobs;
     std::vector<std::pair<double, int2>> items;
     for (MergeReq* r : reqs) {
-        vie_grid* g = r->g;
-        for (size_t i = 0; i < g->groups.size(); ++i) {
-            Group& gr = g->groups[i];
-            if (!gr.fit[pi]) continue;
-            InnerJob<C> j;
-            j.bs = &gr.bs;
-            j.v = group_vecs<C>(gr);
-            j.chi = chi_of<C>(gr.bs);
-            j.G = spec_of<C>(r->sp, 1 + (int)i);
-            j.st = gr.st;
-            if (pi == 1 && !slab_disabled()) j.Go = reinterpret_cast<const C*>(r->sp->go64[1 + i]);
-            const int job = (int)jobs.size();
-            jobs.push_back(j);
-            // longest first: the block's iterations in its last application x its padded box size
-            for (int b = 0; b < gr.bs.nb; ++b)
-                items.push_back({(gr.last_iters[pi][b] + 1.0) * (double)gr.bs.spec_elems(), make_int2(job, b)});
-        }
+        const int off = (int)jobs.size();
+        const std::vector<InnerJob<C>>& rj = req_jobs<C>(r);
+        jobs.insert(jobs.end(), rj.begin(), rj.end());
+        for (const auto& it : r->items) items.push_back({it.first, make_int2(it.second.x + off, it.second.y)});
     }
-    if (jobs.empty()) return VIE_OK;
+    if (jobs.empty() || items.empty()) return VIE_OK;
     VIE_TRY(merge_capacity(mc, (int64_t)jobs.size(), (int64_t)items.size()));
     std::stable_sort(items.begin(), items.end(), [](const std::pair<double, int2>& a, const std::pair<double, int2>& b) {
         return a.first > b.first;
@@ -899,22 +838,22 @@ static void merge_flush(MergeCtx* mc) {
     mc->cv.notify_all();
 }
 
-static void merge_join(MergeMember* mm) {
+void merge_join(MergeMember* mm) {
     MergeCtx* mc = mm->ctx;
     std::lock_guard<std::mutex> lock(mc->m);
     mc->live++;
     mm->live = true;
 }
 
-static void merge_arrive(MergeMember* mm, MergeReq* r) {
+void merge_arrive(MergeMember* mm, MergeReq* r) {
     MergeCtx* mc = mm->ctx;
     std::lock_guard<std::mutex> lock(mc->m);
     mc->pending.push_back(r);
     if ((int)mc->pending.size() >= mc->live) merge_flush(mc);
 }
 
-// Waits (on the host) until the launch holding r is queued; the solve's stream then waits for it.
-static int merge_wait(MergeMember* mm, MergeReq* r, cudaStream_t s) {
+// Waits (on the host) until the launch holding r is queued; the member's stream then waits for it.
+int merge_wait(MergeMember* mm, MergeReq* r, cudaStream_t s) {
     MergeCtx* mc = mm->ctx;
     std::unique_lock<std::mutex> lock(mc->m);
     mc->cv.wait(lock, [&] { return r->gen != -1; });
@@ -929,13 +868,38 @@ static int merge_wait(MergeMember* mm, MergeReq* r, cudaStream_t s) {
     return VIE_OK;
 }
 
-static void merge_leave(MergeMember* mm) {
+void merge_leave(MergeMember* mm) {
     if (!mm || !mm->live) return;
     MergeCtx* mc = mm->ctx;
     std::lock_guard<std::mutex> lock(mc->m);
     mm->live = false;
     mc->live--;
     if (!mc->pending.empty() && (int)mc->pending.size() >= mc->live) merge_flush(mc);
+}
+
+// The grid's jobs and work items for a merged launch: every group that fits, each block costed by
+// its iterations in its last application x its padded box.
+template <class C>
+static void grid_merge_jobs(vie_grid* g, const vie_spectrum* sp, MergeReq* r) {
+    const int pi = prec_of<C>() == VIE_C128 ? 0 : 1;
+    std::vector<InnerJob<C>>& jobs = req_jobs<C>(r);
+    jobs.clear();
+    r->items.clear();
+    for (size_t i = 0; i < g->groups.size(); ++i) {
+        Group& gr = g->groups[i];
+        if (!gr.fit[pi]) continue;
+        InnerJob<C> j;
+        j.bs = &gr.bs;
+        j.v = group_vecs<C>(gr);
+        j.chi = chi_of<C>(gr.bs);
+        j.G = spec_of<C>(sp, 1 + (int)i);
+        j.st = gr.st;
+        if (pi == 1 && !slab_disabled()) j.Go = reinterpret_cast<const C*>(sp->go64[1 + i]);
+        const int job = (int)jobs.size();
+        jobs.push_back(j);
+        for (int b = 0; b < gr.bs.nb; ++b)
+            r->items.push_back({(gr.last_iters[pi][b] + 1.0) * (double)gr.bs.spec_elems(), make_int2(job, b)});
+    }
 }
 
 // y = K2^{-1} b: all blocks of all groups iterate together; a block stops
@@ -988,8 +952,7 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     } guard{mm, &req, s};
     if (merged && any_fit) {
         VIE_CK(cudaEventRecord(g->fork_ev, s));
-        req.g = g;
-        req.sp = sp;
+        grid_merge_jobs<C>(g, sp, &req);
         req.prec = c128 ? 0 : 1;
         req.tol = tol;
         req.maxit = maxit;

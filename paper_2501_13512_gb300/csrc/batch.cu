@@ -12,6 +12,8 @@
 #include <chrono>
 #include <cmath>
 #include <map>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "vie_internal.cuh"
@@ -39,6 +41,7 @@ struct vie_batch {
     bool persistent = false;
     double* h_scal = nullptr;             // pinned [2 count]
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_ready = nullptr;       // gathers queued before a merged launch
     std::map<double, std::pair<double2*, float2*>> spectra;   // cached per wavenumber
     std::vector<void*> allocations;
     int64_t device_bytes = 0;
@@ -65,6 +68,7 @@ void release(vie_batch* b) {
     for (void* p : b->allocations) dfree(p);
     if (b->h_scal) cudaFreeHost(b->h_scal);
     if (b->ev) cudaEventDestroy(b->ev);
+    if (b->ev_ready) cudaEventDestroy(b->ev_ready);
     delete b;
 }
 
@@ -221,7 +225,8 @@ extern "C" int vie_batch_create(const vie_batch_desc* d, vie_batch** out) {
     }
     if (cudaHostAlloc((void**)&b->h_scal, 2 * d->count * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
         return bail(fail(VIE_ENOMEM, "vie_batch_create: pinned allocation failed"));
-    if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_ready, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(VIE_ECUDA, "vie_batch_create: event creation failed"));
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(VIE_ECUDA, "vie_batch_create: set-up failed"));
     *out = b;
@@ -239,8 +244,21 @@ extern "C" int vie_batch_destroy(vie_batch* b) {
     return VIE_OK;
 }
 
+namespace vie {
+static int batch_solve_impl(vie_batch* b, const double* k0s, const void* einc_dev, void* e_dev,
+                            const vie_solve_opts* o, cudaStream_t s, vie_solve_stats* stats, MergeMember* mm);
+}
+
 extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc_dev, void* e_dev,
                                const vie_solve_opts* o, vie_stream_t stream, vie_solve_stats* stats) {
+    return batch_solve_impl(b, k0s, einc_dev, e_dev, o, (cudaStream_t)stream, stats, nullptr);
+}
+
+namespace vie {
+// The batched mixed solve; mm (may be null): membership in a merge session, whose merged launches
+// then take this batch's persistent correction launches.
+static int batch_solve_impl(vie_batch* b, const double* k0s, const void* einc_dev, void* e_dev,
+                            const vie_solve_opts* o, cudaStream_t s, vie_solve_stats* stats, MergeMember* mm) {
     if (!b || !k0s || !einc_dev || !e_dev || !o) return fail(VIE_EINVAL, "vie_batch_solve: null argument");
     if (o->mode != VIE_MODE_MIXED) return fail(VIE_EINVAL, "vie_batch_solve: only VIE_MODE_MIXED is supported");
     if (o->x0_dev) return fail(VIE_EINVAL, "vie_batch_solve: x0_dev must be NULL");
@@ -253,7 +271,6 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
     if (ea < xa + nv * 16 && xa < ea + nv * 16) return fail(VIE_EINVAL, "vie_batch_solve: einc and e overlap");
     for (int i = 0; i < nb; ++i)
         if (!(k0s[i] > 0.0) || !std::isfinite(k0s[i])) return fail(VIE_EINVAL, "vie_batch_solve: k0 must be positive");
-    cudaStream_t s = (cudaStream_t)stream;
     const double tmo = o->wait_timeout_ms;
     BoxSet& bs = b->bs;
     // spectra per distinct wavenumber (cached), one pointer per instance
@@ -370,8 +387,23 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
             jobs[0].st = b->st;
             jobs[0].Gb = b->d_gb64;
             jobs[0].tols = b->d_tols;
-            VIE_TRY(inner_persistent<float2>(jobs, b->work, nb, b->inner_groups, b->inner_next, 0.5,
-                                             o->outer_maxit, s));
+            if (mm != nullptr && mm->live) {
+                // the corrections of every batch of the session that reached this step, in one launch
+                MergeReq req;
+                req.prec = 1;
+                req.tol = 0.5;
+                req.maxit = o->outer_maxit;
+                req.j64 = jobs;
+                for (int i = 0; i < nb; ++i)
+                    if (tols[i] > 0.0) req.items.push_back({(double)bs.spec_elems(), make_int2(0, i)});
+                VIE_CK(cudaEventRecord(b->ev_ready, s));
+                req.ready = b->ev_ready;
+                merge_arrive(mm, &req);
+                VIE_TRY(merge_wait(mm, &req, s));
+            } else {
+                VIE_TRY(inner_persistent<float2>(jobs, b->work, nb, b->inner_groups, b->inner_next, 0.5,
+                                                 o->outer_maxit, s));
+            }
         } else {
             Bicg<float2> k;
             k.nseg = nb;
@@ -425,6 +457,84 @@ extern "C" int vie_batch_solve(vie_batch* b, const double* k0s, const void* einc
         if (status[i] != VIE_OK) {
             set_error("vie_batch_solve: some instances did not reach the tolerance");
             return VIE_ENOTCONV;
+        }
+    return VIE_OK;
+}
+}  // namespace vie
+
+// Several batches (any grid shapes) at once in a session of their own: one host thread and stream
+// per batch, the persistent correction launches of all batches at the same refinement step merged.
+extern "C" int vie_batch_solve_many(int32_t n, vie_batch* const* batches, const double* const* k0s,
+                                    const void* const* einc_dev, void* const* e_dev, const vie_solve_opts* opts,
+                                    vie_stream_t stream, vie_solve_stats* const* stats, vie_merge_stats* merge) {
+    if (n < 1 || !batches || !k0s || !einc_dev || !e_dev || !opts)
+        return fail(VIE_EINVAL, "vie_batch_solve_many: null argument or n < 1");
+    if (merge) memset(merge, 0, sizeof(*merge));
+    for (int i = 0; i < n; ++i) {
+        if (!batches[i]) return fail(VIE_EINVAL, "vie_batch_solve_many: null batch");
+        for (int j = 0; j < i; ++j)
+            if (batches[j] == batches[i]) return fail(VIE_EINVAL, "vie_batch_solve_many: a batch appears twice");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 1) return batch_solve_impl(batches[0], k0s[0], einc_dev[0], e_dev[0], &opts[0], s,
+                                        stats ? stats[0] : nullptr, nullptr);
+    vie_merge_session* mc = nullptr;
+    VIE_TRY(vie_merge_session_create(&mc));
+    std::vector<cudaStream_t> st(n, nullptr);
+    cudaEvent_t start = nullptr;
+    cudaError_t ce = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventRecord(start, s);
+    for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+        ce = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st[i], start, 0);
+    }
+    auto cleanup = [&]() {
+        for (auto x : st)
+            if (x) cudaStreamDestroy(x);
+        if (start) cudaEventDestroy(start);
+        vie_merge_session_destroy(mc);
+    };
+    if (ce != cudaSuccess) {
+        const int rc = cuda_fail(ce, "vie_batch_solve_many: stream set-up", __FILE__, __LINE__);
+        cleanup();
+        return rc;
+    }
+    std::vector<MergeMember> mm(n);
+    for (int i = 0; i < n; ++i) {
+        mm[i].ctx = mc;
+        if (batches[i]->persistent) merge_join(&mm[i]);
+    }
+    std::vector<int> rcs(n, VIE_OK);
+    std::vector<std::string> errs(n);
+    auto run = [&](int i) {
+        cudaError_t e = cudaSetDevice(batches[i]->device);
+        int r = e == cudaSuccess ? batch_solve_impl(batches[i], k0s[i], einc_dev[i], e_dev[i], &opts[i], st[i],
+                                                    stats ? stats[i] : nullptr, &mm[i])
+                                 : cuda_fail(e, "cudaSetDevice", __FILE__, __LINE__);
+        merge_leave(&mm[i]);
+        if (r != VIE_OK) errs[i] = last_error_message();
+        rcs[i] = r;
+    };
+    {
+        std::vector<std::thread> th;
+        th.reserve(n);
+        for (int i = 0; i < n; ++i) th.emplace_back(run, i);
+        for (auto& t : th) t.join();
+    }
+    if (merge) vie_merge_session_stats(mc, merge);
+    for (int i = 0; i < n; ++i) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, st[i]);
+            cudaStreamWaitEvent(s, ev, 0);
+            cudaEventDestroy(ev);
+        }
+    }
+    cleanup();
+    for (int i = 0; i < n; ++i)
+        if (rcs[i] != VIE_OK) {
+            set_error("vie_batch_solve_many: batch " + std::to_string(i) + ": " + errs[i]);
+            return rcs[i];
         }
     return VIE_OK;
 }

@@ -4,7 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <condition_variable>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/vie.h"
@@ -13,6 +17,7 @@ namespace vie {
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
+std::string last_error_message();   // this thread's last error message
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
@@ -360,6 +365,64 @@ int inner_persistent(const std::vector<InnerJob<C>>& jobs, const int2* d_work, i
                      int* d_next, double tol, int maxit, cudaStream_t s, int cluster = 0,
                      const InnerSplit* split = nullptr, int npl = 0);
 int inner_cluster_forced();
+
+// ---------------------------------------------------------------- merge sessions (api.cu)
+// Solves (or batched solves) that run at the same time, one host thread and one stream each,
+// inside one session. A member's persistent block-solver launch is replaced by a request: the
+// member queues its gathers, records `ready` on its stream and arrives; once every live member of
+// the session has arrived, the last to arrive queues ONE persistent launch over the jobs of all
+// requests (one per precision, tolerance and iteration limit) on the session's stream, and each
+// member's stream waits for it (merge_wait) before using the results. Each block's work is the
+// same as in a launch of its own.
+struct MergeReq {
+    int prec = 0;                                   // 0: complex128, 1: complex64
+    double tol = 0.0;
+    int maxit = 0;
+    std::vector<InnerJob<double2>> j128;            // the member's jobs (prec 0)
+    std::vector<InnerJob<float2>> j64;              // (prec 1)
+    std::vector<std::pair<double, int2>> items;     // (cost, (job within the member's jobs, box))
+    cudaEvent_t ready = nullptr;
+    int64_t gen = -1;                               // launch that took it (-1: none yet, -2: failed)
+};
+struct MergeLaunch {
+    cudaEvent_t done = nullptr;
+    int waiting = 0;                                // members that have not yet waited for it
+};
+}  // namespace vie
+
+struct vie_merge_session {
+    std::mutex m;
+    std::condition_variable cv;
+    int device = 0;
+    int live = 0;                  // members that may still arrive
+    int inside = 0;                // vie_solve_merged calls running in the session
+    std::vector<vie::MergeReq*> pending;
+    cudaStream_t ms = nullptr;     // every merged launch, in order
+    std::map<int64_t, vie::MergeLaunch> launches_open;
+    std::vector<cudaEvent_t> free_events;
+    int64_t next_gen = 0;
+    char* d_groups = nullptr;      // group descriptors of a launch
+    int2* d_work = nullptr;        // (job, box) work list of a launch
+    int* d_next = nullptr;
+    int64_t groups_cap = 0, work_cap = 0;
+    std::vector<void*> retired;    // outgrown buffers (a queued launch may still read them)
+    int launches = 0;
+    int64_t members = 0;
+    int max_members = 0;
+    std::string err;
+};
+
+namespace vie {
+using MergeCtx = vie_merge_session;
+// One member's membership: it leaves (once) when it stops launching block solves.
+struct MergeMember {
+    MergeCtx* ctx = nullptr;
+    bool live = false;
+};
+void merge_join(MergeMember* mm);
+void merge_arrive(MergeMember* mm, MergeReq* r);
+int merge_wait(MergeMember* mm, MergeReq* r, cudaStream_t s);
+void merge_leave(MergeMember* mm);
 // True when the environment variable VIE_INNER_SLAB is 0: complex64 blocks keep the register-FFT MVM
 // instead of the slab MVM (read once).
 bool slab_disabled();

@@ -122,6 +122,8 @@ def load(path=LIB_PATH):
         "vie_batch_destroy": ([P], c_int),
         "vie_batch_solve": ([P, POINTER(c_double), P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
         "vie_batch_get_info": ([P, POINTER(c_int64), POINTER(c_int32)], c_int),
+        "vie_batch_solve_many": ([c_int32, POINTER(P), POINTER(P), POINTER(P), POINTER(P), POINTER(SolveOpts), P,
+                                  POINTER(P), POINTER(MergeStats)], c_int),
         "vie_profile_enable": ([c_int], c_int),
         "vie_profile_read": ([POINTER(KernelStat), c_int, POINTER(c_int), POINTER(c_int64)], c_int),
         "vie_rooftop_create": ([P, c_double, c_int, P, POINTER(P)], c_int),
@@ -497,14 +499,17 @@ class Batch:
             raise ValueError("einc must be a complex128 CUDA tensor of shape (count, 3, nz, ny, nx)")
         e = self.empty() if e is None else e
         k = (c_double * self.count)(*[float(v) for v in np.broadcast_to(np.asarray(k0s, float), (self.count,))])
-        o = SolveOpts(float(outer_tol), 0.0, int(outer_maxit), 1, 0, MODE_MIXED, int(max_refinements),
-                      float(wait_timeout_ms))
+        o = self._opts(outer_tol, outer_maxit, max_refinements, wait_timeout_ms)
         st = (SolveStats * self.count)()
         rc = load().vie_batch_solve(self.handle, k, c_void_p(einc.data_ptr()), c_void_p(e.data_ptr()), byref(o),
                                     _stream(), st)
         if check:
             _check(rc, allow=(VIE_ENOTCONV,))
         return e, [_struct_dict(x) for x in st]
+
+    def _opts(self, outer_tol=1e-6, outer_maxit=1000, max_refinements=0, wait_timeout_ms=0.0):
+        return SolveOpts(float(outer_tol), 0.0, int(outer_maxit), 1, 0, MODE_MIXED, int(max_refinements),
+                         float(wait_timeout_ms))
 
     def close(self):
         if self.handle:
@@ -516,3 +521,41 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def batch_solve_many(jobs, check=True):
+    """Solves several batches (vie_batch_solve_many) of different grid shapes together: each job is a dict
+    with keys batch, k0s, einc, optionally e, and options of Batch.solve. The persistent correction launches
+    of all batches run merged. Returns ([(e, [stats per instance]) per job], merge stats)."""
+    import torch
+    n = len(jobs)
+    bh = (c_void_p * n)()
+    kp = (c_void_p * n)()
+    ein = (c_void_p * n)()
+    eout = (c_void_p * n)()
+    opts = (SolveOpts * n)()
+    stp = (c_void_p * n)()
+    keep = []
+    out = []
+    for i, j in enumerate(jobs):
+        b = j["batch"]
+        einc = j["einc"]
+        if tuple(einc.shape) != (b.count, 3) + b.shape or einc.dtype != torch.complex128 or not einc.is_cuda:
+            raise ValueError("einc must be a complex128 CUDA tensor of shape (count, 3, nz, ny, nx)")
+        e = j.get("e")
+        e = b.empty() if e is None else e
+        k = (c_double * b.count)(*[float(v) for v in np.broadcast_to(np.asarray(j["k0s"], float), (b.count,))])
+        st = (SolveStats * b.count)()
+        keep += [k, st]
+        bh[i] = _addr(b.handle)
+        kp[i] = ctypes.cast(k, c_void_p).value
+        ein[i] = einc.data_ptr()
+        eout[i] = e.data_ptr()
+        opts[i] = b._opts(**{k_: v for k_, v in j.items() if k_ not in ("batch", "k0s", "einc", "e")})
+        stp[i] = ctypes.cast(st, c_void_p).value
+        out.append((e, st))
+    ms = MergeStats()
+    rc = load().vie_batch_solve_many(n, bh, kp, ein, eout, opts, _stream(), stp, byref(ms))
+    if check:
+        _check(rc, allow=(VIE_ENOTCONV,))
+    return [(e, [_struct_dict(x) for x in st]) for e, st in out], _struct_dict(ms)

@@ -54,3 +54,30 @@ def test_batch_identical_instances_agree_and_zero_rhs():
     e = e.cpu().numpy()
     assert np.array_equal(e[0], e[1]) and np.array_equal(e[0], e[3])   # same work, same bits
     assert not np.any(e[2]) and stats[2]["status"] == vie.VIE_OK
+
+
+def test_batches_of_several_sizes_share_launches():
+    # vie_batch_solve_many: batches of 12^3, 16^3 and 24^3 instances at once, their corrections merged into
+    # one persistent launch per refinement step; each instance's FP64 residual (oracle operator) meets the
+    # tolerance and its field equals the batch solved alone up to rounding
+    specs = [(12, 3), (16, 2), (24, 2)]
+    jobs, alone, cases = [], [], []
+    for n, count in specs:
+        ws, k0s, eincs = _instances(n, count, seed0=7 * n)
+        ein = torch.from_numpy(np.stack(eincs)).cuda()
+        jobs.append({"batch": vie.Batch([w.eps_r for w in ws], ws[0].h), "k0s": k0s, "einc": ein, "outer_tol": 1e-6})
+        alone.append(vie.Batch([w.eps_r for w in ws], ws[0].h))
+        cases.append((ws, k0s, eincs))
+    res, ms = vie.batch_solve_many(jobs)
+    assert ms["launches"] >= 1 and ms["max_solves"] == 3
+    for (e, stats), job, b1, (ws, k0s, eincs) in zip(res, jobs, alone, cases):
+        e1, _ = b1.solve(k0s, job["einc"], outer_tol=1e-6)
+        torch.cuda.synchronize()
+        e, e1 = e.cpu().numpy(), e1.cpu().numpy()
+        for i, (w, k, inc) in enumerate(zip(ws, k0s, eincs)):
+            assert stats[i]["status"] == vie.VIE_OK
+            res_i = np.linalg.norm(inc - omvm.FFTOperator(w.eps_r, w.h, k)(e[i])) / np.linalg.norm(inc)
+            assert res_i <= 1.05e-6, (w.n, i, res_i)
+            assert np.linalg.norm(e[i] - e1[i]) <= 1e-5 * np.linalg.norm(e1[i])
+    with pytest.raises(vie.VieError):
+        vie.batch_solve_many([jobs[0], dict(jobs[0])])             # a batch listed twice
