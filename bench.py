@@ -581,7 +581,7 @@ def main():
     far_field = {"directions": len(th), "ms": t_ff * 1e3, "directions_per_s": len(th) / t_ff,
                  "note": "vie_far_field_rcs on the solved metasurface field, FP64, host-timed incl. read-back"}
 
-    # end to end through the host-buffer API: pinned E_inc in, E out, copies inside the timed region
+    # end to end through the host-buffer C call (vie_solve_host): pinned E_inc in, E out, copies inside the timed region
     e2e = None
     if args.e2e_steps > 0:
         h_in = einc.cpu().pin_memory()

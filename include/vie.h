@@ -241,6 +241,18 @@ int vie_solve(vie_grid* grid, const vie_spectrum* spectrum, const void* einc_dev
               void* e_dev, const vie_solve_opts* opts, vie_stream_t stream,
               vie_solve_stats* stats);
 
+/* vie_solve from HOST buffers: einc_host (read) and e_host (written), complex128
+ * [3][nz][ny][nx] in host memory (pinned memory lets the copies run at full
+ * speed; pageable memory works too), distinct. E_inc is copied to a device
+ * vector of the grid, solved there as by vie_solve (opts->x0_dev, if set, is a
+ * DEVICE vector), and E copied back on `stream`; returns after E has landed in
+ * e_host (also for VIE_ENOTCONV, whose E is valid). The grid keeps the two
+ * device vectors (2 x 48 N bytes, allocated on the first call, counted in
+ * device_bytes and the device budget). Errors as vie_solve. */
+int vie_solve_host(vie_grid* grid, const vie_spectrum* spectrum, const void* einc_host,
+                   void* e_host, const vie_solve_opts* opts, vie_stream_t stream,
+                   vie_solve_stats* stats);
+
 /* ---- Solves of many requests with merged block-solver launches. ----
  * Serving runs the solves of several requests at once, each on its own grid
  * (any shapes, modes and tolerances), host thread and stream. Inside a merge

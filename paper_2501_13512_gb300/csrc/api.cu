@@ -1406,6 +1406,27 @@ static int solve_impl(vie_grid* g, const vie_spectrum* sp, const void* einc, voi
 
 }  // namespace vie
 
+// A solve from host buffers: E_inc copied in and E copied out on `stream` around the solve, through
+// two device vectors the grid keeps (allocated on first use).
+extern "C" int vie_solve_host(vie_grid* g, const vie_spectrum* sp, const void* einc_host, void* e_host,
+                              const vie_solve_opts* o, vie_stream_t stream, vie_solve_stats* stats) {
+    if (!g || !einc_host || !e_host || !o) return fail(VIE_EINVAL, "vie_solve_host: null argument");
+    const int64_t bytes = 3 * g->N * (int64_t)sizeof(double2);
+    if (overlaps(einc_host, e_host, bytes)) return fail(VIE_EINVAL, "vie_solve_host: einc and e overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto& p : g->host_io)
+        if (!p) VIE_TRY(dalloc(g, &p, 3 * g->N));
+    VIE_CK(cudaMemcpyAsync(g->host_io[0], einc_host, bytes, cudaMemcpyHostToDevice, s));
+    const int rc = solve_impl(g, sp, g->host_io[0], g->host_io[1], o, s, stats, nullptr);
+    if (rc != VIE_OK && rc != VIE_ENOTCONV) return rc;
+    const std::string msg = rc == VIE_OK ? std::string() : g_last_error;
+    VIE_CK(cudaMemcpyAsync(e_host, g->host_io[1], bytes, cudaMemcpyDeviceToHost, s));
+    VIE_CK(cudaEventRecord(g->ev[0], s));
+    VIE_TRY(wait_event(g->ev[0], o->wait_timeout_ms));
+    if (rc != VIE_OK) set_error(msg);
+    return rc;
+}
+
 // ---------------------------------------------------------------- merge sessions
 extern "C" int vie_merge_session_create(vie_merge_session** out) {
     if (!out) return fail(VIE_EINVAL, "vie_merge_session_create: null argument");

@@ -218,6 +218,7 @@ struct vie_grid {
     vie::KrylovVecs<float2> o64;
     double2* tmp128 = nullptr;            // full-grid scratch vector
     double2* x0buf = nullptr;             // plain solves warm-started in place (allocated on first use)
+    double2* host_io[2] = {nullptr, nullptr};   // vie_solve_host: E_inc and E on the device (first use)
     float2* tmp64 = nullptr;
     vie::SegState* ost = nullptr;         // outer state [1]
     vie::ReduceScratch ored;

@@ -110,6 +110,7 @@ def load(path=LIB_PATH):
         "vie_matvec": ([P, P, c_int, P, P, P], c_int),
         "vie_block_precond_apply": ([P, P, c_int, P, P, c_double, c_int, P, POINTER(PrecondStats)], c_int),
         "vie_solve": ([P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
+        "vie_solve_host": ([P, P, P, P, POINTER(SolveOpts), P, POINTER(SolveStats)], c_int),
         "vie_merge_session_create": ([POINTER(P)], c_int),
         "vie_merge_session_destroy": ([P], c_int),
         "vie_merge_session_stats": ([P, POINTER(MergeStats)], c_int),
@@ -347,70 +348,25 @@ class Grid:
                                         _stream()))
         return out
 
-    def solve_host(self, spec, einc_host, out_host, **kw):
-        """End-to-end solve from pinned host memory: H2D copy, solve, D2H copy."""
+    def solve_host(self, spec, einc_host, out_host, outer_tol=1e-6, inner_tol=1e-2, outer_maxit=1000,
+                   inner_maxit=1000, use_precond=True, mode=MODE_MIXED, max_refinements=0, wait_timeout_ms=0.0,
+                   check=True):
+        """End-to-end solve from host memory (vie_solve_host): einc_host and out_host are contiguous complex128
+        CPU tensors of shape (3, nz, ny, nx) (pinned for full-speed copies); E_inc in, E out, both copies
+        inside the call."""
         import torch
-        dev = torch.empty((3,) + self.shape, dtype=torch.complex128, device="cuda")
-        dev.copy_(einc_host, non_blocking=True)
-        e, st = self.solve(spec, dev, **kw)
-        out_host.copy_(e, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return out_host, st
-
-
-class MergeSession:
-    """Solves run concurrently (own threads and streams) inside a session share persistent block-solver
-    launches (vie_merge_session_*)."""
-
-    def __init__(self):
-        h = c_void_p()
-        _check(load().vie_merge_session_create(byref(h)))
-        self.handle = h
-
-    def stats(self):
-        ms = MergeStats()
-        _check(load().vie_merge_session_stats(self.handle, byref(ms)))
-        return _struct_dict(ms)
-
-    def close(self):
-        if self.handle:
-            _check(load().vie_merge_session_destroy(self.handle))
-            self.handle = None
-
-
-def _addr(p):
-    return p.value if isinstance(p, c_void_p) else p
-
-
-def solve_many(problems, check=True):
-    """Solves several systems at once (vie_solve_many): each problem is a dict with keys grid, spec, einc,
-    optionally e, and any option of Grid.solve (outer_tol, inner_tol, mode, ...); the grids must be distinct.
-    Block-preconditioner applications of all solves share persistent launches. Returns
-    ([(e, stats) per problem], merge stats)."""
-    n = len(problems)
-    grids = (c_void_p * n)()
-    specs = (c_void_p * n)()
-    ein = (c_void_p * n)()
-    eout = (c_void_p * n)()
-    opts = (SolveOpts * n)()
-    stats = (SolveStats * n)()
-    fields = []
-    for i, p in enumerate(problems):
-        g = p["grid"]
-        e = p.get("e")
-        e = g.empty(C128) if e is None else e
-        fields.append(e)
-        kw = {k: v for k, v in p.items() if k not in ("grid", "spec", "einc", "e")}
-        grids[i] = _addr(g.handle)
-        specs[i] = _addr(p["spec"].handle)
-        ein[i] = _addr(g._vec(p["einc"], C128, "einc"))
-        eout[i] = _addr(g._vec(e, C128, "e"))
-        opts[i] = g._opts(**kw)
-    ms = MergeStats()
-    rc = load().vie_solve_many(n, grids, specs, ein, eout, opts, _stream(), stats, byref(ms))
-    if check:
-        _check(rc, allow=(VIE_ENOTCONV,))
-    return [(fields[i], _struct_dict(stats[i])) for i in range(n)], _struct_dict(ms)
+        for t, name in ((einc_host, "einc_host"), (out_host, "out_host")):
+            if (not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.complex128
+                    or tuple(t.shape) != (3,) + self.shape or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous complex128 CPU tensor of shape {(3,) + self.shape}")
+        o = self._opts(outer_tol, inner_tol, outer_maxit, inner_maxit, use_precond, mode, max_refinements,
+                       wait_timeout_ms)
+        st = SolveStats()
+        rc = load().vie_solve_host(self.handle, spec.handle, c_void_p(einc_host.data_ptr()),
+                                   c_void_p(out_host.data_ptr()), byref(o), _stream(), byref(st))
+        if check:
+            _check(rc, allow=(VIE_ENOTCONV,))
+        return out_host, _struct_dict(st)
 
 
 class Rooftop:
