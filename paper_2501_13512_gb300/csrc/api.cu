@@ -962,26 +962,31 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
     }
     bool slab = false;
     for (const InnerJob<C>& j : jobs) slab = slab || j.Go != nullptr;
-    // launch shape, tuned on the first applies, then the best. Register-FFT MVM: 2 and 4 CTAs per
-    // block, then the split launch (the slowest blocks of the previous apply on 4 CTAs, the rest on 2).
-    // Slab MVM (whole MVM on chip, the cluster splits the kz planes): 2, 1 and 4 CTAs with 4 planes per
-    // round where they fit, then 2 CTAs with 2 planes per round (a split cannot shorten the slowest
-    // block's solve, which bounds the apply once every block fits on the device at once).
-    // candidates (CTAs per block, kz planes per round of the slab MVM's plane stage; 0 = as many as fit)
+    // launch shape and MVM variant, tuned on the first applies, then the best. Register-FFT MVM: 2 and
+    // 4 CTAs per block, then the split launch (the slowest blocks of the previous apply on 4 CTAs, the
+    // rest on 2). Blocks the slab MVM takes (whole MVM on chip, the cluster splits the kz planes): 2, 1
+    // and 4 CTAs with 4 planes per round where they fit, 2 CTAs with 2 planes per round (a split cannot
+    // shorten the slowest block's solve, which bounds the apply once every block fits on the device at
+    // once), and the register-FFT MVM with 2 CTAs instead of the slab MVM.
+    // candidates (CTAs per block, kz planes per round of the slab MVM's plane stage with 0 = as many as
+    // fit, slab MVM or register MVM)
     struct Cand {
         int cluster, npl;
+        bool slab;
     };
-    static const Cand kCand[3] = {{2, 0}, {4, 0}, {-1, 0}};
-    static const Cand kCandSlab[4] = {{2, 4}, {1, 4}, {4, 4}, {2, 2}};
-    const int ncand = slab ? 4 : 3;
+    static const Cand kCand[3] = {{2, 0, false}, {4, 0, false}, {-1, 0, false}};
+    static const Cand kCandSlab[5] = {{2, 4, true}, {1, 4, true}, {4, 4, true}, {2, 2, true}, {2, 0, false}};
+    const int ncand = slab ? 5 : 3;
     const int pi = c128 ? 0 : 1;
     // the first apply only warms up (first launches of the kernel pay one-time costs that would bias
     // the candidate tried first); the candidates follow, one per apply
     const int tried = g->tune_count[pi] - 1;
     const bool tuning = !jobs.empty() && tried < ncand && !inner_cluster_forced();
     const Cand cand = tuning ? (slab ? kCandSlab : kCand)[std::max(tried, 0)]
-                             : Cand{g->tune_best[pi] ? g->tune_best[pi] : 2, g->tune_npl[pi]};
+                             : Cand{g->tune_best[pi] ? g->tune_best[pi] : 2, g->tune_npl[pi], !g->tune_noslab[pi]};
     const int choice = cand.cluster;
+    if (slab && !cand.slab)
+        for (InnerJob<C>& j : jobs) j.Go = nullptr;   // the register-FFT MVM for these blocks
     // with batched groups as well, the persistent launch runs on the grid's second stream beside
     // the batched steps (no split launch then)
     const bool beside = !jobs.empty() && !batched.empty();
@@ -1123,6 +1128,7 @@ static int precond_apply(vie_grid* g, const vie_spectrum* sp, const C* b, C* y, 
                 if (g->tune_score[pi][k] < g->tune_score[pi][best]) best = k;
             g->tune_best[pi] = (slab ? kCandSlab : kCand)[best].cluster;
             g->tune_npl[pi] = (slab ? kCandSlab : kCand)[best].npl;
+            g->tune_noslab[pi] = slab && !kCandSlab[best].slab;
         }
     }
     return VIE_OK;

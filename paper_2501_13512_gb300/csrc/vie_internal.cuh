@@ -242,7 +242,8 @@ struct vie_grid {
     int tune_count[2] = {0, 0};
     int tune_best[2] = {0, 0};
     int tune_npl[2] = {0, 0};             // slab MVM: kz planes per round of the best candidate (0: auto)
-    double tune_score[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    bool tune_noslab[2] = {false, false}; // the best candidate ran the register-FFT MVM instead of the slab MVM
+    double tune_score[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
     int nheavy[2] = {0, 0};               // blocks of the split launch's heavy part (from the last apply)
     cudaEvent_t tev[2] = {nullptr, nullptr};
     int64_t device_bytes = 0;

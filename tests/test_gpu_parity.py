@@ -272,10 +272,10 @@ def test_solve_rejects_overlapping_x0():
 
 
 def test_precond_every_tuner_candidate_meets_inner_tolerance():
-    # the first apply of a persistent grid warms up, the next ones run the launch-shape candidates (slab
-    # MVM: 2, 1 and 4 CTAs per block with 4 kz planes per round, 2 CTAs with 2 planes; register MVM: 2,
-    # 4 and the split launch), the sixth the chosen one; every block of every apply meets the inner
-    # tolerance
+    # the first apply of a persistent grid warms up, the next ones run the tuner's candidates (blocks of
+    # the slab MVM: 2, 1 and 4 CTAs per block with 4 kz planes per round, 2 CTAs with 2 planes, and the
+    # register MVM on 2 CTAs; other blocks: 2, 4 and the split launch), the seventh the chosen one;
+    # every block of every apply meets the inner tolerance
     w = inputs.metasurface(cells=4, seed=3)
     rng = np.random.default_rng(8)
     b = rng.normal(size=(3,) + w.eps_r.shape) + 1j * rng.normal(size=(3,) + w.eps_r.shape)
@@ -284,7 +284,7 @@ def test_precond_every_tuner_candidate_meets_inner_tolerance():
     bb = b.astype(np.complex64).astype(np.complex128)
     blocks = oprecond.find_blocks(w.block_id)
     ops = [omvm.FFTOperator(w.eps_r[blk.slices], w.h, w.k0, mask=blk.mask) for blk in blocks]
-    for apply in range(6):
+    for apply in range(7):
         y, st = g.precond(sp, dev(b, torch.complex64), inner_tol=1e-2)
         assert st["nblocks"] == 16 and st["not_converged"] == 0 and st["breakdowns"] == 0
         y = host(y)
