@@ -369,6 +369,67 @@ class Grid:
         return out_host, _struct_dict(st)
 
 
+class MergeSession:
+    """Solves run concurrently (own threads and streams) inside a session share persistent block-solver
+    launches (vie_merge_session_*)."""
+
+    def __init__(self):
+        h = c_void_p()
+        _check(load().vie_merge_session_create(byref(h)))
+        self.handle = h
+
+    def stats(self):
+        ms = MergeStats()
+        _check(load().vie_merge_session_stats(self.handle, byref(ms)))
+        return _struct_dict(ms)
+
+    def close(self):
+        if self.handle:
+            _check(load().vie_merge_session_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _addr(p):
+    return p.value if isinstance(p, c_void_p) else p
+
+
+def solve_many(problems, check=True):
+    """Solves several systems at once (vie_solve_many): each problem is a dict with keys grid, spec, einc,
+    optionally e, and any option of Grid.solve (outer_tol, inner_tol, mode, ...); the grids must be distinct.
+    Block-preconditioner applications of all solves share persistent launches. Returns
+    ([(e, stats) per problem], merge stats)."""
+    n = len(problems)
+    grids = (c_void_p * n)()
+    specs = (c_void_p * n)()
+    ein = (c_void_p * n)()
+    eout = (c_void_p * n)()
+    opts = (SolveOpts * n)()
+    stats = (SolveStats * n)()
+    fields = []
+    for i, p in enumerate(problems):
+        g = p["grid"]
+        e = p.get("e")
+        e = g.empty(C128) if e is None else e
+        fields.append(e)
+        kw = {k: v for k, v in p.items() if k not in ("grid", "spec", "einc", "e")}
+        grids[i] = _addr(g.handle)
+        specs[i] = _addr(p["spec"].handle)
+        ein[i] = _addr(g._vec(p["einc"], C128, "einc"))
+        eout[i] = _addr(g._vec(e, C128, "e"))
+        opts[i] = g._opts(**kw)
+    ms = MergeStats()
+    rc = load().vie_solve_many(n, grids, specs, ein, eout, opts, _stream(), stats, byref(ms))
+    if check:
+        _check(rc, allow=(VIE_ENOTCONV,))
+    return [(fields[i], _struct_dict(stats[i])) for i in range(n)], _struct_dict(ms)
+
+
 class Rooftop:
     """The paper's rooftop / pulse discretisation of a grid's permittivity (vie_rooftop): unknown
     w = J / (j w eps0) on faces, vectors (3, nz, ny, nx) with component a at the face above cell c."""

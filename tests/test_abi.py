@@ -86,3 +86,12 @@ def test_argument_validation_without_gpu():
     assert lib.vie_matvec_noalloc(17, 17, 17, 1.0, 1.0, buf, buf, buf, None) == vie.VIE_EINVAL
     assert "exceeds" in vie.last_error()
     assert lib.vie_matvec_noalloc(4, 4, 4, 1.0, 1.0, None, buf, buf, None) == vie.VIE_EINVAL
+
+
+def test_python_binding_exposes_every_public_wrapper():
+    # the ctypes binding's public wrappers of the merge-session, batch and host-buffer entry points exist
+    from paper_2501_13512_gb300 import vie
+    for name in ("Grid", "Spectrum", "Batch", "Rooftop", "MergeSession", "solve_many", "batch_solve_many"):
+        assert hasattr(vie, name), name
+    for meth in ("solve", "solve_host", "precond", "matvec", "spectrum", "plane_wave", "far_field_rcs"):
+        assert hasattr(vie.Grid, meth), meth
