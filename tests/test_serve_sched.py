@@ -90,3 +90,38 @@ def test_server_survives_a_failing_request():
         bad.result(timeout=30)
     assert ok.result(timeout=30).stats["outer_iters"] == 1.0
     srv.close()
+
+
+def test_engine_keeps_one_merge_session_per_grid_size():
+    # the GPU engine's session bookkeeping with a stand-in for the binding's MergeSession (no GPU)
+    from paper_2501_13512_gb300.serve import GpuEngine
+
+    class FakeSession:
+        made = []
+
+        def __init__(self):
+            self.closed = False
+            self.st = {"launches": 3 * (len(FakeSession.made) + 1), "max_solves": 2 + len(FakeSession.made),
+                       "mean_solves": 1.5}
+            FakeSession.made.append(self)
+
+        def stats(self):
+            return dict(self.st)
+
+        def close(self):
+            self.closed = True
+
+    class FakeVie:
+        MergeSession = FakeSession
+
+    eng = GpuEngine(merge=True)
+    eng.vie = FakeVie()
+    a, b, c = _req(8), _req(27), _req(8)
+    sa, sb, sc = eng._session(a), eng._session(b), eng._session(c)
+    assert sa is sc and sa is not sb and len(FakeSession.made) == 2
+    st = eng.merge_stats()
+    assert st["launches"] == 3 + 6 and st["max_solves"] == 3
+    assert abs(st["mean_solves"] - 1.5) < 1e-12
+    eng.close()
+    assert all(s.closed for s in FakeSession.made) and eng.merge_stats()["launches"] == 0
+    assert GpuEngine(merge=False)._session(a) is None
