@@ -687,7 +687,7 @@ constexpr int kSlabThreads = VIE_SLAB_THREADS;
 #endif
 constexpr int kSlabMinBlocks = VIE_SLAB_MINB;
 #ifndef VIE_SLAB_BATCH
-#define VIE_SLAB_BATCH 4
+#define VIE_SLAB_BATCH 1
 #endif
 constexpr int kSlabBatch = VIE_SLAB_BATCH;   // z planes per thread whose global loads are issued together
 
